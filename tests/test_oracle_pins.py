@@ -1,0 +1,540 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a table the
+paper prints (App. B, App. C), a closed form, an algebraic identity of the
+linear theory, a textbook special case, a library routine (numpy.fft, scipy,
+Triton's CPU interpreter for Philox) or a statistical law.  Paper references
+are to Gross, Cates, Varnik & Adhikari, arXiv 1012.3632.
+"""
+import json
+import os
+import subprocess
+import sys
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from oracle import theory
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLD = os.path.join(HERE, "golden")
+CS2 = 1.0 / 3.0
+
+
+def _frac(s):
+    return float(Fraction(s))
+
+
+def _read_blocks(path):
+    blocks, cur = {}, None
+    for line in open(path):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        if line.isalpha():
+            cur = blocks.setdefault(line, [])
+            continue
+        cur.append([_frac(t) for t in line.split()])
+    return {k: np.array(v) for k, v in blocks.items()}
+
+
+# --------------------------------------------------------------------------
+# Random numbers
+# --------------------------------------------------------------------------
+
+_TRITON_SCRIPT = r"""
+import os, json, sys
+os.environ["TRITON_INTERPRET"] = "1"
+import torch, triton, triton.language as tl
+from triton.language.random import philox
+
+@triton.jit
+def k(out_ptr, c_ptr, seed, n: tl.constexpr):
+    off = tl.arange(0, n)
+    c0 = tl.load(c_ptr + off * 4 + 0).to(tl.uint32)
+    c1 = tl.load(c_ptr + off * 4 + 1).to(tl.uint32)
+    c2 = tl.load(c_ptr + off * 4 + 2).to(tl.uint32)
+    c3 = tl.load(c_ptr + off * 4 + 3).to(tl.uint32)
+    a, b, c, d = philox(seed, c0, c1, c2, c3)
+    tl.store(out_ptr + off * 4 + 0, a.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + off * 4 + 1, b.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + off * 4 + 2, c.to(tl.int32, bitcast=True))
+    tl.store(out_ptr + off * 4 + 3, d.to(tl.int32, bitcast=True))
+
+req = json.loads(sys.argv[1])
+ctr = torch.tensor([[x - (1 << 32) if x >= (1 << 31) else x for x in c] for c in req["ctr"]],
+                   dtype=torch.int32)
+n = ctr.shape[0]
+out = torch.zeros(n * 4, dtype=torch.int32)
+k[(1,)](out, ctr, req["seed"], n)
+print(json.dumps([x & 0xFFFFFFFF for x in out.tolist()]))
+"""
+
+
+def test_philox_matches_library(orc):
+    """Philox4x32-10 of the oracle equals the Philox of Triton's CPU interpreter
+    (a library routine; key = (seed lo, seed hi), 10 rounds)."""
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(7)
+    ctrs = [[0, 0, 0, 0], [1, 2, 3, 4], [0xFFFFFFFF] * 4]
+    ctrs += [list(map(int, rng.integers(0, 2**32, 4, dtype=np.uint64))) for _ in range(13)]
+    seed = 0x1234567890ABCDEF
+    r = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT, json.dumps({"ctr": ctrs, "seed": seed})],
+                       capture_output=True, text=True, timeout=600)
+    if r.returncode != 0:
+        pytest.skip("Triton interpreter unavailable: " + r.stderr[-300:])
+    lib = json.loads(r.stdout.strip().splitlines()[-1])
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    mine = []
+    for c in ctrs:
+        mine += orc.philox4x32_10(c, key)
+    assert mine == lib
+
+
+def test_box_muller_is_standard_normal(orc):
+    """The normals drawn for the noise are N(0,1): Kolmogorov-Smirnov against scipy."""
+    stats = pytest.importorskip("scipy.stats")
+    z = np.concatenate([orc.normals4(11, s, 5, b, 0, 3) for s in range(3000) for b in range(3)])
+    assert abs(z.mean()) < 0.03
+    assert abs(z.var() - 1.0) < 0.03
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------
+# Lattices and bases
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_weights_are_isotropic(orc, Q):
+    """sum w = 1, sum w c c = cs^2 delta, sum w cccc = cs^4 (dd + dd + dd): the
+    conditions behind Eq. (feq) with cs^2 = 1/3 (Sec. III)."""
+    L = orc.lattice(Q)
+    D = L.D
+    c = L.c[:, :D].astype(float)
+    assert np.isclose(L.w.sum(), 1.0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib->ab", L.w, c, c), CS2 * np.eye(D), atol=1e-15)
+    assert np.allclose(np.einsum("i,ia->a", L.w, c), 0, atol=1e-15)
+    assert np.allclose(np.einsum("i,ia,ib,ic->abc", L.w, c, c, c), 0, atol=1e-15)
+    I = np.eye(D)
+    iso = CS2**2 * (np.einsum("ab,cd->abcd", I, I) + np.einsum("ac,bd->abcd", I, I)
+                    + np.einsum("ad,bc->abcd", I, I))
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", L.w, c, c, c, c), iso, atol=1e-15)
+
+
+def test_d2q9_table_I(orc):
+    """Printed D2Q9 basis (App. B): the N_a of Table I satisfy Eq. (T-orthog) and
+    Eq. (T-complete) with the oracle's T and w, and T f^eq gives the m^eq column."""
+    L = orc.lattice(9)
+    rows = [l.split() for l in open(os.path.join(GOLD, "d2q9_table1.txt")) if l.strip() and not l.startswith("#")]
+    Nprint = np.array([_frac(r[1]) for r in rows])
+    G = (L.T * L.w) @ L.T.T
+    assert np.allclose(G, np.diag(Nprint), atol=1e-14)
+    comp = (L.w[:, None] * L.T.T / Nprint) @ L.T
+    assert np.allclose(comp, np.eye(9), atol=1e-14)
+    # velocities are rows 2-3 of T
+    assert np.array_equal(L.c[:, 0], L.T[1]) and np.array_equal(L.c[:, 1], L.T[2])
+    rng = np.random.default_rng(3)
+    p = orc.Params(Q=9, dims=(1, 1, 1), omega_shear=0, omega_bulk=0, omega_ghost=0)
+    for _ in range(5):
+        rho = 1 + 0.2 * rng.standard_normal()
+        ux, uy = 0.05 * rng.standard_normal(2)
+        # kT = 0 and all rates 1 -> f* = f^eq; so T f* = m^eq (F = 0)
+        fin = orc.init(p, rho=[rho], u=[[ux], [uy]])[:, 0]
+        m = L.T @ fin
+        expect = [eval(r[2], {}, dict(rho=rho, ux=ux, uy=uy)) for r in rows]
+        assert np.allclose(m, expect, atol=1e-14)
+
+
+def _d3q19_closed_forms():
+    rows = [l.split() for l in open(os.path.join(GOLD, "d3q19_basis_closed_forms.txt"))
+            if l.strip() and not l.startswith("#")]
+    return rows
+
+
+def test_d3q19_basis_closed_forms(orc):
+    """Gram-Schmidt basis of the oracle equals the hand-derived polynomials and
+    norms, and T f^eq equals the hand-derived equilibrium moments (ghosts 0,
+    which is the property of the weighted basis stated after Eq. (T-complete))."""
+    L = orc.lattice(19)
+    rows = _d3q19_closed_forms()
+    for a, r in enumerate(rows):
+        vals = [eval(r[1], {}, dict(x=c[0], y=c[1], z=c[2], c2=float(c @ c))) for c in L.c.astype(float)]
+        assert np.allclose(L.T[a], vals, atol=1e-14), a
+        assert np.isclose(L.N[a], _frac(r[2]), atol=1e-15), a
+    rng = np.random.default_rng(5)
+    p = orc.Params(Q=19, dims=(1, 1, 1))
+    for _ in range(5):
+        rho = 1 + 0.2 * rng.standard_normal()
+        u = 0.05 * rng.standard_normal(3)
+        f = orc.init(p, rho=[rho], u=u.reshape(3, 1))[:, 0]
+        m = L.T @ f
+        env = dict(rho=rho, ux=u[0], uy=u[1], uz=u[2])
+        assert np.allclose(m, [eval(r[3], {}, env) for r in rows], atol=1e-14)
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_basis_orthogonal_complete(orc, Q):
+    """Eqs. (T-orthog) and (T-complete) by brute force; rank Q; the first 1+D+D(D+1)/2
+    vectors span {1, c_a, c_a c_b} (Sec. III)."""
+    L = orc.lattice(Q)
+    G = (L.T * L.w) @ L.T.T
+    assert np.allclose(G, np.diag(L.N), atol=1e-14)
+    assert np.allclose(L.Tinv @ L.T, np.eye(Q), atol=1e-14)
+    assert np.linalg.matrix_rank(L.T) == Q
+    D = L.D
+    nh = 1 + D + D * (D + 1) // 2
+    c = L.c[:, :D].astype(float)
+    polys = [np.ones(Q)] + [c[:, a] for a in range(D)] + [c[:, a] * c[:, b] for a in range(D) for b in range(a, D)]
+    P = np.array(polys)
+    coef, *_ = np.linalg.lstsq(L.T[:nh].T, P.T, rcond=None)
+    assert np.allclose(L.T[:nh].T @ coef, P.T, atol=1e-13)
+    # classes: d+1 conserved, d(d+1)/2 stress, the rest ghosts (Sec. III)
+    assert (L.cls == 0).sum() == D + 1
+    assert ((L.cls == 1) | (L.cls == 2)).sum() == D * (D + 1) // 2
+    assert (L.cls == 1).sum() == 1
+
+
+def test_advection_matrix_app_C(orc):
+    """T diag(c.k) T^-1 with (T^-1)_ib = w_i T_bi / N_b reproduces the printed
+    D2Q9 advection operator of App. C, Eq. (adv-op)."""
+    L = orc.lattice(9)
+    g = _read_blocks(os.path.join(GOLD, "d2q9_advection_appC.txt"))
+    for k in ([1.0, 0.0], [0.0, 1.0], [0.3, -0.7]):
+        A = theory.advection(L, k)
+        assert np.allclose(A, -1j * (k[0] * g["AX"] + k[1] * g["AY"]), atol=1e-14)
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_ideal_gas_advection_antisymmetry(orc, Q):
+    """A G = -G A^dagger for the ideal-gas G (Sec. IV.A)."""
+    L = orc.lattice(Q)
+    G = theory.G_ideal(L, 1.0, 1e-4)
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        A = theory.advection(L, rng.uniform(-np.pi, np.pi, L.D))
+        assert np.allclose(A @ G, -G @ A.conj().T, atol=1e-18)
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_fdt_noise_ideal_and_force_model(orc, Q):
+    """Eq. (dbe-fdt) gives Xi = 2 Lambda G for the ideal gas (Eq. (noise-ideal)) and
+    for the force-based model (Eq. (noise-nonideal)) at any k: the advective and
+    force contributions cancel, and Xi vanishes on the conserved modes."""
+    L = orc.lattice(Q)
+    rng = np.random.default_rng(2)
+    rho0, kT = 1.0, 1e-5
+    for _ in range(6):
+        k = rng.uniform(-np.pi, np.pi, L.D)
+        lam = theory.relaxation(L, *rng.uniform(0.2, 3.0, 3))
+        A = theory.advection(L, k)
+        Gi = theory.G_ideal(L, rho0, kT)
+        Xi = theory.fdt_noise(A + lam, Gi)
+        assert np.allclose(Xi, 2 * lam @ Gi, atol=1e-18)
+        cs2k = CS2 - 0.01 + 0.02 * (k @ k)
+        Gf = theory.G_force(L, rho0, kT, cs2k)
+        K = theory.K_force(L, k, cs2k)
+        Xf = theory.fdt_noise(A + lam - K, Gf)
+        assert np.allclose(Xf, 2 * lam @ Gf, atol=1e-18)
+        assert np.allclose(Xf[: L.D + 1, :], 0, atol=1e-18)
+
+
+def test_lattice_noise_from_dbe_noise(orc):
+    """Eq. (noise-lbe) equals (1 - omega/2)^2 times the DBE covariance 2 lambda G of
+    Eq. (noise-ideal) under lambda^LB = 2 lambda / (2 + lambda) (Sec. V)."""
+    L = orc.lattice(19)
+    for om in (0.3, 1.0, 1.2, 1.7):
+        lam = theory.lambda_dbe(om)
+        assert np.isclose(theory.lambda_lb(lam), om)
+        for a in range(4, 19):
+            dbe = 2 * lam * 1.0 * (1e-5 / CS2) * L.N[a]
+            assert np.isclose((1 - om / 2) ** 2 * dbe, theory.lattice_noise_variance(L, 1.0, 1e-5, om, a))
+
+
+# --------------------------------------------------------------------------
+# Collision
+# --------------------------------------------------------------------------
+
+def _bgk_guo(L, f, F, om):
+    """Textbook BGK collision with Guo forcing in population space:
+    f* = f - om (f - f^eq) + (1 - om/2) w_i [(c_i - u).F / cs2 + (c_i.u)(c_i.F)/cs2^2],
+    u = (sum f c + F/2)/rho."""
+    c = L.c.astype(float)
+    rho = f.sum()
+    u = (f @ c + 0.5 * F) / rho
+    cu = c @ u
+    feq = L.w * rho * (1 + cu / CS2 + cu**2 / (2 * CS2**2) - (u @ u) / (2 * CS2))
+    phi = L.w * (((c - u) @ F) / CS2 + cu * (c @ F) / CS2**2)
+    return f - om * (f - feq) + (1 - om / 2) * phi
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_mrt_reduces_to_bgk(orc, Q):
+    """With one rate for every non-conserved mode and kT = 0 the moment-space
+    update Eq. (lbe-mom) is the BGK update with Guo forcing (Sec. III, BGK case)."""
+    L = orc.lattice(Q)
+    rng = np.random.default_rng(Q)
+    for om in (0.6, 1.0, 1.5):
+        p = orc.Params(Q=Q, dims=(4, 4, 1 if Q == 9 else 4), omega_shear=om, omega_bulk=om, omega_ghost=om)
+        for _ in range(4):
+            f = L.w * (1 + 0.1 * rng.standard_normal(Q))
+            F = np.zeros(3)
+            F[: L.D] = 1e-3 * rng.standard_normal(L.D)
+            got = orc.collide_site(p, f, F, 5, 3)
+            assert np.allclose(got, _bgk_guo(L, f, F, om), atol=1e-15)
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_forcing_moments(orc, Q):
+    """With all rates 0 the update adds exactly the force moments m^F, which are
+    {0, F, u_a F_b + F_a u_b on the stress modes, 0 on the ghosts} (Eqs.
+    (force-mom), (lbe-moments)); the stress part is the m^eq closed form with
+    rho u_a u_b replaced by u_a F_b + F_a u_b."""
+    L = orc.lattice(Q)
+    rng = np.random.default_rng(10 + Q)
+    p = orc.Params(Q=Q, dims=(3, 3, 1 if Q == 9 else 3), omega_shear=0, omega_bulk=0, omega_ghost=0)
+    for _ in range(4):
+        f = L.w * (1 + 0.1 * rng.standard_normal(Q))
+        F = np.zeros(3)
+        F[: L.D] = 1e-2 * rng.standard_normal(L.D)
+        mF = L.T @ (orc.collide_site(p, f, F, 0, 0) - f)
+        c = L.c.astype(float)
+        u = (f @ c + 0.5 * F) / f.sum()
+        # stress part from the D-dimensional tensor (uF + Fu) projected on the stress modes
+        S = np.outer(u, F) + np.outer(F, u)
+        # m_a = sum_i T_ai w_i S_ab Q_iab / (2 cs2^2): same map that takes rho u u to m^eq
+        Qt = np.einsum("ia,ib->iab", c, c) - CS2 * np.eye(3)
+        expect = L.T @ (L.w * np.einsum("iab,ab->i", Qt, S) / (2 * CS2**2))
+        expect[1: 1 + L.D] = F[: L.D]
+        # f* - f cancels to ~1e-16 of f ~ 0.3: compare at that rounding level
+        assert np.allclose(mF, expect, atol=4e-15)
+        assert np.allclose(mF[L.cls == 3], 0, atol=4e-15)
+        assert abs(mF[0]) < 4e-15
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_single_site_fdt_is_exactly_stationary(orc, Q):
+    """Lattice FDT, Eq. (noise-lbe): around the rest state the linearised collision
+    J plus the noise the oracle adds keeps the ideal-gas equal-time covariance
+    G_f = mu rho0 w_i delta_ij (Eqs. (f-correl-ideal), (mu-ideal)) exactly:
+    J G_f J^T + C_noise = G_f.  The noise covariance is read off one noisy
+    collision by dividing each mode's noise by the normal it was drawn from."""
+    L = orc.lattice(Q)
+    rho0, kT = 1.0, 1e-4
+    oms = dict(omega_shear=1.3, omega_bulk=0.7, omega_ghost=1.55)
+    p0 = orc.Params(Q=Q, dims=(2, 2, 1 if Q == 9 else 2), kT=0.0, rho0=rho0, seed=9, **oms)
+    f0 = L.w * rho0
+    eps = 1e-6
+    J = np.zeros((Q, Q))
+    for n in range(Q):
+        d = np.zeros(Q)
+        d[n] = eps
+        J[:, n] = (orc.collide_site(p0, f0 + d, [0, 0, 0], 1, 4) - orc.collide_site(p0, f0 - d, [0, 0, 0], 1, 4)) / (2 * eps)
+    pn = p0.with_(kT=kT)
+    xi = L.T @ (orc.collide_site(pn, f0, [0, 0, 0], 1, 4) - orc.collide_site(p0, f0, [0, 0, 0], 1, 4))
+    nnc = Q - 1 - L.D
+    z = np.concatenate([orc.normals4(9, 1, 4, b, 0, 0) for b in range((nnc + 3) // 4)])[:nnc]
+    s = np.zeros(Q)
+    s[L.D + 1:] = xi[L.D + 1:] / z
+    assert np.allclose(xi[: L.D + 1], 0, atol=1e-16)
+    Cn = L.Tinv @ np.diag(s**2) @ L.Tinv.T
+    Gf = (kT / CS2) * rho0 * np.diag(L.w)
+    assert np.allclose(J @ Gf @ J.T + Cn, Gf, rtol=0, atol=1e-9 * Gf.max())
+
+
+# --------------------------------------------------------------------------
+# Whole steps
+# --------------------------------------------------------------------------
+
+def _sums(L, f):
+    c = L.c.astype(float)
+    return f.sum(), (c.T @ f).sum(axis=1)
+
+
+def test_conservation_ideal(orc):
+    """Noise has no conserved component (Sec. IV.A): total mass and momentum are
+    constant to rounding over many steps."""
+    L = orc.lattice(19)
+    p = orc.Params(Q=19, dims=(6, 5, 4), kT=1e-4, omega_shear=1.3, omega_bulk=0.9, omega_ghost=1.4, seed=4)
+    f = orc.init(p, thermal=True, u=np.full((3, p.V), 0.01))
+    m0, j0 = _sums(L, f)
+    f = orc.run(p, f, 0, 150)
+    m1, j1 = _sums(L, f)
+    assert abs(m1 - m0) < 1e-13 * m0
+    assert np.allclose(j1, j0, atol=1e-13 * m0)
+
+
+def test_conservation_nonideal(orc):
+    """Force model: mass is exact; the total momentum grows by the total force
+    each step (the Guo term adds F to j, Eq. (lbe-mom))."""
+    L = orc.lattice(19)
+    rng = np.random.default_rng(8)
+    p = orc.Params(Q=19, dims=(5, 6, 4), kT=1e-5, nonideal=True, A=-0.01, B=0.1, kappa=0.02, seed=2)
+    rho = 1 + 0.01 * rng.uniform(-1, 1, p.V)
+    f = orc.init(p, rho=rho)
+    for t in range(20):
+        m0, j0 = _sums(L, f)
+        _, F = orc.density_force(p, f)
+        f = orc.step(p, f, t)
+        m1, j1 = _sums(L, f)
+        assert abs(m1 - m0) < 1e-13 * m0
+        assert np.allclose(j1 - j0, F.sum(axis=1), atol=1e-14)
+
+
+def test_noise_free_rest_state_is_fixed(orc):
+    """kT = 0 reduces to deterministic MRT-LB: a uniform rest state is a fixed point."""
+    for Q, dims in ((9, (5, 4, 1)), (19, (3, 4, 5))):
+        L = orc.lattice(Q)
+        p = orc.Params(Q=Q, dims=dims, omega_shear=1.4, omega_bulk=0.8, omega_ghost=1.2)
+        f = orc.init(p)
+        g = orc.run(p, f, 0, 25)
+        assert np.allclose(g, f, rtol=0, atol=1e-15)
+        assert np.allclose(f, np.repeat(L.w[:, None], p.V, 1), atol=1e-16)
+
+
+def test_nonideal_with_zero_free_energy_equals_ideal(orc):
+    """kappa = A = B = 0 makes the force vanish: bitwise the ideal-gas update."""
+    p = orc.Params(Q=19, dims=(4, 3, 5), kT=1e-4, omega_shear=1.2, seed=3)
+    f = orc.init(p, thermal=True)
+    a = orc.run(p, f, 7, 10)
+    b = orc.run(p.with_(nonideal=True, A=0.0, B=0.0, kappa=0.0), f, 7, 10)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_shear_wave_decay(orc, Q):
+    """Shear-wave amplitude decays as exp(-nu k^2 t), nu = cs^2 (1/omega - 1/2)
+    (App. B viscosity with the lambda^LB map of Sec. V); 128-site wave."""
+    Lz = 128
+    om = 1.2
+    dims = (1, Lz, 1) if Q == 9 else (1, 1, Lz)
+    p = orc.Params(Q=Q, dims=dims, omega_shear=om, omega_bulk=1.0, omega_ghost=1.0)
+    D = 2 if Q == 9 else 3
+    s = np.arange(Lz)
+    u = np.zeros((D, Lz))
+    u[0] = 1e-5 * np.sin(2 * np.pi * s / Lz)
+    f = orc.init(p, u=u)
+    L = orc.lattice(Q)
+    amp = []
+    t_meas = [300, 2300]
+    t = 0
+    for tm in t_meas:
+        f = orc.run(p, f, t, tm - t)
+        t = tm
+        jx = L.c[:, 0] @ f
+        amp.append(abs(np.fft.fft(jx)[1]))
+    rate = np.log(amp[0] / amp[1]) / (t_meas[1] - t_meas[0])
+    k = 2 * np.pi / Lz
+    expect = theory.shear_viscosity(om) * k * k
+    assert abs(rate / expect - 1) < 5e-3
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_force_stencils_reduce_to_central_differences(orc, Q):
+    """For a density varying along x only, the isotropic lattice stencils reduce to
+    the textbook 3-point Laplacian and central difference, so
+    F = -rho * D0[psi'(rho) - kappa D2 rho] (App. A force, F = -rho grad mu)."""
+    X = 24
+    dims = (X, 1, 1)
+    A, B, rc, kap = -0.01, 0.1, 1.0, 0.02
+    p = orc.Params(Q=Q, dims=dims, nonideal=True, A=A, B=B, rho_c=rc, kappa=kap)
+    x = np.arange(X)
+    rho = 1.0 + 0.05 * np.cos(2 * np.pi * 3 * x / X) + 0.02 * np.sin(2 * np.pi * x / X)
+    f = orc.init(p, rho=rho)
+    r, F = orc.density_force(p, f)
+    assert np.allclose(r, rho, atol=1e-15)
+    d2 = np.roll(rho, -1) - 2 * rho + np.roll(rho, 1)
+    mu = A * (rho - rc) + B * (rho - rc) ** 3 - kap * d2
+    Fx = -rho * (np.roll(mu, -1) - np.roll(mu, 1)) / 2
+    assert np.allclose(F[0], Fx, atol=1e-15)
+    assert np.allclose(F[1:], 0, atol=1e-17)
+
+
+def test_window_matches_full_lattice(orc):
+    """A window of the periodic lattice evolves like the full lattice inside its
+    light cone (used for sampled parity at full size)."""
+    p = orc.Params(Q=19, dims=(12, 11, 10), kT=1e-4, nonideal=True, A=-0.01, B=0.1, kappa=0.02, seed=6)
+    rng = np.random.default_rng(4)
+    rho = 1 + 0.01 * rng.uniform(-1, 1, p.V)
+    f = orc.init(p, rho=rho, thermal=True)
+    full = orc.run(p, f, 0, 2)
+    org, win = (3, 2, 1), (9, 9, 8)
+    f4 = f.reshape(19, 10, 11, 12)
+    fw = np.ascontiguousarray(f4[:, org[2]:org[2] + win[2], org[1]:org[1] + win[1], org[0]:org[0] + win[0]]).reshape(19, -1)
+    pw = p.with_(origin=org, window=win)
+    got = orc.run(pw, fw, 0, 2).reshape(19, win[2], win[1], win[0])
+    want = full.reshape(19, 10, 11, 12)[:, org[2]:org[2] + win[2], org[1]:org[1] + win[1], org[0]:org[0] + win[0]]
+    r = 2 * 3  # two steps, cone radius 3 per step with the force stencils
+    core = (slice(None), slice(r, win[2] - r), slice(r, win[1] - r), slice(r, win[0] - r))
+    assert np.array_equal(got[core], want[core])
+    assert np.isnan(got[:, 0, 0, 0]).any()
+
+
+# --------------------------------------------------------------------------
+# Statistics of the fluctuating update (FDT)
+# --------------------------------------------------------------------------
+
+def _mode_temperatures(L, p, f_samples):
+    """T_a = cs^2 <dm_a^2> / (rho0 N_a), dm = deviation from the site mean."""
+    T = np.zeros(L.Q)
+    for f in f_samples:
+        m = L.T @ f
+        dm = m - m.mean(axis=1, keepdims=True)
+        T += (dm**2).mean(axis=1)
+    T /= len(f_samples)
+    return CS2 * T / (p.rho0 * L.N)
+
+
+@pytest.mark.parametrize("Q,dims,steps", [(9, (16, 16, 1), 3000), (19, (6, 6, 6), 1600)])
+def test_mode_temperatures_equal_kT(orc, Q, dims, steps):
+    """Every mode, ghosts included, equilibrates at the noise temperature
+    (Eqs. (G-ideal), (noise-lbe)): T_a = kT within statistics."""
+    L = orc.lattice(Q)
+    kT = 1e-5
+    p = orc.Params(Q=Q, dims=dims, kT=kT, omega_shear=1.3, omega_bulk=0.8, omega_ghost=1.5, seed=12)
+    f = orc.init(p, thermal=True)
+    samples = []
+    t = 0
+    f = orc.run(p, f, t, 100)
+    t = 100
+    while t < steps:
+        f = orc.run(p, f, t, 10)
+        t += 10
+        samples.append(f.copy())
+    Ta = _mode_temperatures(L, p, samples) / kT
+    # density and momentum: k = 0 removed by the site mean -> (V-1)/V of kT
+    Ta[: L.D + 1] *= p.V / (p.V - 1.0)
+    assert np.all(np.abs(Ta - 1) < 0.04), Ta
+
+
+def test_thermal_init_variances(orc):
+    """Thermal initial state: every mode has variance rho0 kT N_a / cs^2 (Eq. (G-ideal))."""
+    Q = 19
+    L = orc.lattice(Q)
+    kT = 1e-5
+    p = orc.Params(Q=Q, dims=(16, 16, 16), kT=kT, seed=21)
+    f = orc.init(p, thermal=True)
+    Ta = _mode_temperatures(L, p, [f]) / kT
+    assert np.all(np.abs(Ta - 1) < 0.08), Ta
+
+
+# --------------------------------------------------------------------------
+# Structure factor
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(5,), (4, 6), (3, 5, 4), (8, 8, 8)])
+def test_dft_matches_numpy(orc, shape):
+    rng = np.random.default_rng(len(shape))
+    phi = rng.standard_normal(shape)
+    assert np.allclose(orc.dft(phi), np.fft.fftn(phi), atol=1e-11)
+
+
+def test_structure_factor_matches_numpy(orc):
+    """S_a(k) = |DFT(m_a - <m_a>)|^2 / V against numpy.fft on the oracle's modes."""
+    p = orc.Params(Q=19, dims=(6, 5, 4), kT=1e-4, seed=3)
+    f = orc.init(p, thermal=True)
+    m = orc.modes(p, f)
+    for a in (0, 1, 7, 18):
+        d = (m[a] - m[a].mean()).reshape(4, 5, 6)
+        want = np.abs(np.fft.fftn(d)) ** 2 / p.V
+        assert np.allclose(orc.structure_factor(p, f, a).reshape(4, 5, 6), want, atol=1e-15)
