@@ -1,0 +1,340 @@
+"""Benchmark of the fluctuating lattice Boltzmann step on GB300.
+
+Default workload: D3Q19 force-based non-ideal fluid on a 256^3 periodic lattice
+in FP32 deviation storage (A=-0.01, B=0.1, rho_c=1, kappa=0.02, kT=1e-6, all
+relaxation rates 1, rho = 1 + U(-0.01, 0.01) from a seeded generator).  One
+"step" is one full time step of the hot path: the density gather plus the fused
+pull / MRT collide / force / Langevin-noise / store kernel.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun, one rank per GPU) every
+rank advances its own independent replica (distinct Philox replica word):
+weak scaling, no data-path collective.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 fluctuating-LB MLUPS & % HBM roofline; batched/adjoint vs plain step"
+UNIT = "MLUPS"
+FE = dict(A=-0.01, B=0.1, rho_c=1.0, kappa=0.02)
+WORKLOADS = {
+    "nonideal256": dict(lattice=19, dims=(256, 256, 256), precision="fp32", fe=FE, kT=1e-6,
+                        omega=(1.0, 1.0, 1.0), seed=3,
+                        name="D3Q19 force-based non-ideal fluid, 256^3 periodic, FP32 deviations, "
+                             "psi=A(rho-rho_c)^2/2+B(rho-rho_c)^4/4 (A=-0.01, B=0.1, rho_c=1), kappa=0.02, "
+                             "F=-rho grad mu (19-point stencils), Guo forcing, kT=1e-6, omega_shear=1, "
+                             "rho=1+U(-0.01,0.01)"),
+    "ideal128": dict(lattice=19, dims=(128, 128, 128), precision="fp32", fe=None, kT=1e-5,
+                     omega=(1.2, 1.0, 1.0), seed=2,
+                     name="D3Q19 ideal gas, 128^3 periodic, FP32 deviations, kT=1e-5, "
+                          "omega=(1.2, 1.0, 1.0), shear wave + thermal start"),
+}
+# Algorithmic bytes per site of the fused step kernel: 19 pulled + 19 stored
+# populations (+ the density of the site for the non-ideal fluid); of the
+# density gather: 19 pulled populations + 1 density written.
+ELEM = {"fp32": 4, "fp64": 8, "bf16": 2}
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def step_bytes(wl):
+    e = ELEM[wl["precision"]]
+    Q = wl["lattice"]
+    rb = 8 if wl["precision"] == "fp64" else 4
+    fused = 2 * Q * e + (rb if wl["fe"] else 0)
+    gather = Q * e + rb
+    return fused, gather
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1012_3632_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(wl_key):
+    """DRAM bytes per launch of the fused kernel from the committed ncu summary,
+    or None when missing or taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{wl_key}.json")
+    try:
+        j = json.load(open(p))
+    except Exception:
+        return None
+    if j.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return j.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={CLOCK_FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(wl, budget_s=12.0):
+    """Time the FP64 oracle (single thread) on a periodic 64^3 (D3Q19) lattice with
+    the workload's parameters; steps are added until about budget_s of CPU work."""
+    import numpy as np
+
+    import oracle
+    from paper_1012_3632_gb300 import inputs
+
+    dims = (64, 64, 64)
+    om = wl["omega"]
+    fe = wl["fe"] or {}
+    p = oracle.Params(Q=wl["lattice"], dims=dims, omega_shear=om[0], omega_bulk=om[1], omega_ghost=om[2],
+                      kT=wl["kT"], nonideal=bool(wl["fe"]), seed=wl["seed"], **fe)
+    rho = inputs.uniform_density(dims, seed=wl["seed"]) if wl["fe"] else None
+    f = oracle.init(p, rho=rho, thermal=not wl["fe"])
+    t0 = time.perf_counter()
+    steps = 0
+    while time.perf_counter() - t0 < budget_s or steps == 0:
+        f = oracle.step(p, f, steps)
+        steps += 1
+    dt = time.perf_counter() - t0
+    V = int(np.prod(dims))
+    return {"value": V * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{dims[0]}x{dims[1]}x{dims[2]} periodic lattice, same parameters, {steps} steps, "
+                      f"FP64 C oracle, single thread"}
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    from paper_1012_3632_gb300 import inputs
+
+    dims = (64, 64, 64)
+    om = wl["omega"]
+    fe = wl["fe"] or {}
+    p = oracle.Params(Q=wl["lattice"], dims=dims, omega_shear=om[0], omega_bulk=om[1], omega_ghost=om[2],
+                      kT=wl["kT"], nonideal=bool(wl["fe"]), seed=wl["seed"], **fe)
+    rho = inputs.uniform_density(dims, seed=wl["seed"]) if wl["fe"] else None
+    f = oracle.init(p, rho=rho, thermal=not wl["fe"])
+    for t in range(args.warmup):
+        f = oracle.step(p, f, t)
+    t0 = time.perf_counter()
+    for t in range(args.steps):
+        f = oracle.step(p, f, args.warmup + t)
+    dt = time.perf_counter() - t0
+    V = int(np.prod(dims))
+    value = V * args.steps / dt / 1e6
+    sample = f"{dims[0]}x{dims[1]}x{dims[2]} periodic lattice per step, same parameters, FP64 C oracle, 1 thread"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_of(args, wl),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def config_of(args, wl):
+    V = int(wl["dims"][0] * wl["dims"][1] * wl["dims"][2])
+    buf = V * wl["lattice"] * ELEM[wl["precision"]]
+    return {"workload": wl["name"], "lattice_sites": V, "dims": list(wl["dims"]), "replicas": args.gpus,
+            "parallelism": f"replicas{args.gpus}",
+            "l2": f"inputs larger than L2: two population buffers of {buf / 1e9:.3g} GB each, no flush"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="nonideal256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_1012_3632_gb300 import Context, RHO, inputs
+    from paper_1012_3632_gb300 import build as B
+
+    B.build()
+    stream = torch.cuda.current_stream()
+    om = wl["omega"]
+    dims = wl["dims"]
+    V = dims[0] * dims[1] * dims[2]
+    ctx = Context(wl["lattice"], dims, om[0], om[1], om[2], kT=wl["kT"], free_energy=wl["fe"], seed=wl["seed"],
+                  precision=wl["precision"], replica=rank, stream=stream.cuda_stream, device=local)
+    rho = inputs.uniform_density(dims, seed=wl["seed"]) if wl["fe"] else None
+    u = None if wl["fe"] else inputs.shear_wave(dims, amp=1e-3)
+    ctx.init(rho=rho, u=u, thermal=not wl["fe"])
+
+    # ---- device-resident timing ------------------------------------------
+    ctx.step(args.warmup)
+    ctx.synchronize()
+    ctx.kernel_timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        time.sleep(0.3)
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        ctx.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    kms, kn = ctx.kernel_times()
+    ctx.kernel_timing(False)
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * V * args.steps / (ms_max * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers ---------------------
+    # per run: the initial density field (pinned host -> device) in, K steps,
+    # the density field (device -> pinned host) out.
+    host_in = torch.empty(V, dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty(V, dtype=torch.float64, pin_memory=True).numpy()
+    host_in[:] = rho if rho is not None else 1.0
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    if wl["fe"]:
+        ctx.init(rho=host_in)
+    else:
+        ctx.init(rho=host_in, u=u, thermal=True)
+    ctx.step(args.steps)
+    ctx.moments(RHO, out=host_out)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    te = torch.tensor([t_e2e], device="cuda")
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = world * V * args.steps / float(te.item()) / 1e6
+    bytes_u = 0 if wl["fe"] else 3 * V * 8
+    e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (V * 8 + bytes_u) / args.steps,
+           "d2h_bytes_per_step": V * 8 / args.steps,
+           "what": "flb_init from a pinned host density field, K flb_step calls, flb_moments(RHO) to pinned host"}
+
+    ctx.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    fused_b, gather_b = step_bytes(wl)
+    peak, peak_kind = measured_peak()
+    n_fused = int(kn[1])
+    t_fused = kms[1] / max(n_fused, 1) * 1e-3
+    achieved = fused_b * V / t_fused / 1e9
+    traffic = ncu_traffic(args.workload)
+    n_launch = int(kn[0] + kn[1] + kn[2])
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "bf16": "bf16"}[wl["precision"]],
+        "data": "synthetic", "config": config_of(args, wl),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
+                     "kernel": "k_step (fused pull + MRT collide + force + noise + store)",
+                     "bytes_per_site": fused_b, "sites_per_launch": V,
+                     "avg_launch_ms": t_fused * 1e3},
+        "kernels": {"density_gather": {"launches": int(kn[0]), "avg_ms": kms[0] / max(kn[0], 1),
+                                       "bytes_per_site": gather_b,
+                                       "achieved_gbs": gather_b * V / (kms[0] / max(kn[0], 1) * 1e-3) / 1e9
+                                       if kn[0] else None},
+                    "fused_step": {"launches": n_fused, "avg_ms": kms[1] / max(n_fused, 1)}},
+        "whole_step_gbs": (fused_b + (gather_b if wl["fe"] else 0)) * V / (ms_max / args.steps * 1e-3) / 1e9,
+        "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launch,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl)
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

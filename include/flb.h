@@ -1,0 +1,214 @@
+/*
+ * flb.h -- C ABI of the GB300 fluctuating lattice Boltzmann (FLB) library.
+ *
+ * The library advances the fluctuating lattice Boltzmann equation of
+ * M. Gross, M. E. Cates, F. Varnik and R. Adhikari, "Langevin theory of
+ * fluctuations in the discrete Boltzmann equation" (arXiv 1012.3632) on one
+ * GPU.  One time step is the moment-space update of Sec. V, Eq. (lbe-mom):
+ *
+ *   f^LB_i(r + c_i, t+1) = (T^-1)_ia [ m_a - w_a (m_a - m_a^eq)
+ *                                      + (1 - w_a/2) m^F_a + xi^LB_a ]
+ *
+ * with m_a = T_ai f^LB_i (Eq. (moments)), m^eq from the second-order discrete
+ * Maxwellian (Eq. (feq)), m^F from the forcing term (Eq. (forcing-term), Guo
+ * form), relaxation rates w_a = lambda^LB_a (Sec. V) and Gaussian noise
+ * xi^LB_a on every non-conserved mode with the lattice fluctuation-dissipation
+ * variance of Eq. (noise-lbe):
+ *
+ *   < xi^LB_a xi^LB_b > = rho kT (2 - w_a) w_a N_a / cs^2  delta_ab,  cs^2 = 1/3.
+ *
+ * Optionally the fluid is the force-based non-ideal fluid of Sec. IV.B / App. A:
+ * F = -rho grad mu, mu = psi'(rho) - kappa lap rho, with the excess free energy
+ * psi(rho) = A (rho - rho_c)^2 / 2 + B (rho - rho_c)^4 / 4 and the isotropic
+ * lattice stencils grad phi = 3 sum_i w_i c_i phi(r + c_i),
+ * lap phi = 6 sum_i w_i (phi(r + c_i) - phi(r)).
+ *
+ * Conventions shared by every call:
+ *  - Return value: FLB_OK (0) or a negative FLB_E* code; flb_last_error()
+ *    gives a message for the calling thread's last failure.  No C++
+ *    exception crosses this boundary.
+ *  - Lattice dimensions are (X, Y, Z) with Z = 1 for D2Q9; the site index is
+ *    s = x + X*(y + Y*z) (x fastest); V = X*Y*Z sites.
+ *  - Host arrays passed in or out are owned by the caller and are copied;
+ *    the library never keeps a caller pointer.  The library owns all device
+ *    memory it allocates (flb_create) and frees it in flb_destroy.
+ *  - Populations exchanged with the caller are the paper's pre-collision
+ *    f^LB(r, t) (Eq. (f-aux)) as doubles in the layout f[i*V + s] with the
+ *    velocity order below.
+ *      D2Q9  (App. B, rows 2-3 of Eq. (TD2Q9)):
+ *        (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1) (-1,-1) (1,-1)
+ *      D3Q19:
+ *        (0,0,0) (1,0,0) (-1,0,0) (0,1,0) (0,-1,0) (0,0,1) (0,0,-1)
+ *        (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1)
+ *        (1,0,-1) (-1,0,1) (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1)
+ *  - Moment basis: D2Q9 as printed in App. B (rho, jx, jy, e, pww, pxy, qx,
+ *    qy, eps).  D3Q19 (the paper gives none): weighted Gram-Schmidt of
+ *    1; cx, cy, cz; c^2; 3cx^2-c^2, cy^2-cz^2; cxcy, cycz, czcx; c^2 c (x3);
+ *    (cy^2-cz^2)cx, (cz^2-cx^2)cy, (cx^2-cy^2)cz; c^4; c^2(3cx^2-c^2),
+ *    c^2(cy^2-cz^2) -- modes 0-3 conserved, 4 bulk (omega_bulk), 5-9 shear
+ *    (omega_shear), 10-18 ghosts (omega_ghost).  D2Q9: 0-2 conserved,
+ *    3 bulk, 4-5 shear, 6-8 ghosts.
+ *  - Noise: Philox4x32-10 (Salmon et al., SC'11) with key (seed lo, seed hi)
+ *    and counter (site, step, call | tag << 8, replica); Box-Muller on words
+ *    (0,1) and (2,3) of each call, uniforms (x + 1/2) 2^-32.  Non-conserved
+ *    mode k (counted from 0 in basis order) uses normal k%4 of call k/4.
+ *    Tag 0 is the collision noise, tag 1 the thermal initial state.  Any
+ *    site's noise at any step can be recomputed from (seed, replica, site,
+ *    step).
+ *  - Every call is enqueued on the context's CUDA stream; calls that return
+ *    host data synchronise that stream.  A context must not be used by two
+ *    host threads at once.
+ */
+#ifndef FLB_H
+#define FLB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLB_OK 0
+#define FLB_EINVAL (-1)    /* invalid argument (e.g. omega not in (0,2), kT < 0, dims < 1) */
+#define FLB_ENOMEM (-2)    /* device or host allocation failed */
+#define FLB_ECUDA (-3)     /* a CUDA runtime call failed; see flb_last_error() */
+#define FLB_EDIVERGED (-4) /* non-finite mass or momentum detected after a step */
+#define FLB_ETIMEOUT (-5)  /* reserved: a bounded device-side wait gave up */
+#define FLB_EIO (-6)       /* checkpoint file could not be read or written */
+
+typedef struct flb_ctx flb_ctx;
+
+typedef enum { FLB_D2Q9 = 9, FLB_D3Q19 = 19 } flb_lattice;
+
+/* Storage precision of the populations.  FP64: doubles, all arithmetic in
+ * double.  FP32: deviations g_i = f_i - w_i rho0 stored and computed in float.
+ * BF16: deviations stored as bfloat16, arithmetic in float. */
+typedef enum { FLB_FP64 = 0, FLB_FP32 = 1, FLB_BF16 = 2 } flb_precision;
+
+/* Observables of flb_moments. */
+typedef enum {
+    FLB_RHO = 0,      /* out[V]: rho = sum_i f_i (Eq. (lbe-moments)) */
+    FLB_U = 1,        /* out[D*V]: u = (sum_i f_i c_i + F/2) / rho (Eq. (lbe-moments)) */
+    FLB_MODES = 2,    /* out[Q*V]: m_a = T_ai f_i (Eq. (moments)) */
+    FLB_MODE_VAR = 3  /* out[Q]: adds the current state to the snapshot accumulators and
+                         returns the mean over snapshots of (1/V) sum_r (m_a - <m_a>_r)^2 */
+} flb_observable;
+
+/* Square-gradient free energy of the non-ideal fluid (App. A, Eq. (freeE-funct)),
+ * psi being the excess over the ideal lattice gas.  enabled = 0: ideal gas. */
+typedef struct {
+    int enabled;
+    double A, B, rho_c, kappa;
+} flb_free_energy;
+
+typedef struct {
+    int precision;       /* flb_precision (default FLB_FP32) */
+    double rho0;         /* reference density of the deviation storage (default 1) */
+    uint32_t replica;    /* fourth Philox counter word (default 0) */
+    int noise_rho_local; /* 1 (default): local pre-collision rho in the noise variance
+                            (Sec. VI, local values in inhomogeneous states); 0: rho0 */
+    void* stream;        /* cudaStream_t to enqueue on; NULL: the legacy default stream */
+    int device;          /* CUDA device ordinal; -1 (default): the current device */
+    int check_every;     /* flb_step checks mass/momentum for NaN/Inf every this many
+                            steps (0: never; default 0) */
+} flb_options;
+
+/* Fill *opt with the defaults listed above. */
+void flb_default_options(flb_options* opt);
+
+/* Create a context for a periodic lattice and allocate its device state.
+ *   lattice  FLB_D2Q9 or FLB_D3Q19
+ *   dims     (X, Y, Z), each >= 1; Z must be 1 for D2Q9; X*Y*Z < 2^31
+ *   omega_*  lattice relaxation rates lambda^LB (Sec. V) of the shear, bulk and
+ *            ghost modes, each in (0, 2)
+ *   kT       noise temperature >= 0 (kT = 0: deterministic MRT-LB)
+ *   fe       free energy (NULL or enabled = 0: ideal gas)
+ *   seed     64-bit Philox key
+ *   opt      NULL for defaults
+ * The state is the uniform rest state f = w rho0 at step 0.  Returns
+ * FLB_EINVAL for bad arguments (context not created), FLB_ENOMEM, FLB_ECUDA. */
+int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear,
+               double omega_bulk, double omega_ghost, double kT, const flb_free_energy* fe,
+               uint64_t seed, const flb_options* opt);
+
+/* Set the state to f^eq(rho, u) (Eq. (feq)); with thermal_init != 0 every mode a
+ * (conserved ones included) additionally receives a Gaussian of variance
+ * rho kT N_a / cs^2, the ideal-gas equal-time variance of Eqs. (G-ideal) and
+ * (mu-ideal) (noise tag 1, step 0).  rho: host array of V doubles or NULL (rho0);
+ * u: host array of D*V doubles (u[d*V + s]) or NULL (rest).  Resets the step
+ * counter to 0 and clears the accumulators. */
+int flb_init(flb_ctx* ctx, const double* rho, const double* u, int thermal_init);
+
+/* Advance nsteps >= 0 time steps (Eq. (lbe-mom) + streaming, periodic).  With
+ * check_every > 0, returns FLB_EDIVERGED when the total mass or momentum is no
+ * longer finite. */
+int flb_step(flb_ctx* ctx, int nsteps);
+
+/* Copy an observable of the current pre-collision state into the host array
+ * out (size given with flb_observable).  Synchronises the stream. */
+int flb_moments(flb_ctx* ctx, double* out, int which);
+
+/* Structure factor of mode `mode` (0 = density, giving G_11(k) = S(k) of
+ * Sec. IV, Eq. (g-correl)): S_a(k) = |sum_r dm_a(r) exp(-i k.r)|^2 / V with
+ * dm_a = m_a - <m_a>_r and k = 2 pi (n_x/X, n_y/Y, n_z/Z), computed by an FFT in
+ * double precision; S_a(0) = 0.  With accumulate != 0 the snapshot is added to
+ * the mode's double-precision accumulator and S (host, V doubles indexed like
+ * sites by (n_x, n_y, n_z); may be NULL) receives the mean over all accumulated
+ * snapshots of the mode; with accumulate = 0, S receives the current snapshot
+ * and the accumulator is untouched. */
+int flb_structure_factor(flb_ctx* ctx, double* S, int mode, int accumulate);
+
+/* Number of snapshots accumulated for structure factors of `mode`
+ * (mode = -1: the FLB_MODE_VAR accumulators). */
+int flb_snapshot_count(flb_ctx* ctx, int mode, int* count);
+
+/* Clear every snapshot accumulator. */
+int flb_reset_accumulators(flb_ctx* ctx);
+
+/* Total mass and momentum of the current state, summed on the GPU in double:
+ * out[0] = sum rho, out[1..3] = sum_r sum_i f_i c_i (z component 0 for D2Q9). */
+int flb_conservation(flb_ctx* ctx, double out[4]);
+
+/* Read / write the pre-collision populations f^LB (host, Q*V doubles). */
+int flb_get_populations(flb_ctx* ctx, double* f);
+int flb_set_populations(flb_ctx* ctx, const double* f);
+
+/* Step counter (the time index keying the collision noise). */
+int flb_get_step(flb_ctx* ctx, uint64_t* step);
+int flb_set_step(flb_ctx* ctx, uint64_t step);
+
+/* Enqueue subsequent work on another cudaStream_t (NULL: legacy default stream). */
+int flb_set_stream(flb_ctx* ctx, void* stream);
+
+/* Wait for the context's stream. */
+int flb_synchronize(flb_ctx* ctx);
+
+/* Query sizes: out[0] = Q, out[1] = D, out[2..4] = X, Y, Z, out[5] = precision. */
+int flb_get_info(flb_ctx* ctx, int out[6]);
+
+/* Per-kernel CUDA-event timing of flb_step (off by default).  While enabled,
+ * every kernel that flb_step launches is bracketed by events on the context's
+ * stream.  flb_kernel_times fills ms[k] (total milliseconds) and launches[k]
+ * for k < FLB_NKERNEL_TIMERS: 0 = density gather, 1 = fused stream-collide,
+ * 2 = conservation check.  Enabling or disabling clears the totals. */
+#define FLB_NKERNEL_TIMERS 3
+int flb_kernel_timing(flb_ctx* ctx, int enable);
+int flb_kernel_times(flb_ctx* ctx, double* ms, int* launches);
+
+/* Checkpoint: parameters, step counter, seed, replica and the populations in
+ * the stored precision; a resumed run continues bit for bit. */
+int flb_save(flb_ctx* ctx, const char* path);
+int flb_load(flb_ctx** out, const char* path, const flb_options* opt);
+
+/* Message for an error code / for the calling thread's last failure. */
+const char* flb_error_string(int code);
+const char* flb_last_error(void);
+
+/* Free the context and all its device memory (NULL is ignored). */
+void flb_destroy(flb_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLB_H */

@@ -1,0 +1,417 @@
+// flb_device.cuh -- device building blocks of the fluctuating lattice Boltzmann
+// step: counter-based normals, the hand-derived moment transforms of D2Q9 and
+// D3Q19, and the moment-space collision of Gross, Cates, Varnik & Adhikari
+// (arXiv 1012.3632), Sec. V, Eq. (lbe-mom), with the lattice FDT noise of
+// Eq. (noise-lbe).
+//
+// Populations are handled as deviations g_i = f_i - w_i rho0 from the rest
+// state.  Every non-conserved moment of w_i rho0 vanishes (weighted
+// orthogonality, Eq. (T-orthog)), so only the density moment shifts:
+// rho = rho0 + sum_i g_i.
+//
+// The transforms are written out by hand, pairing each velocity c with -c:
+// even moments use s = g(c) + g(-c), odd moments d = g(c) - g(-c).
+#pragma once
+
+#include <cstdint>
+#include <cuda_bf16.h>
+
+namespace flb {
+
+// ---------------------------------------------------------------------------
+// Storage conversions
+// ---------------------------------------------------------------------------
+template <class R, class S>
+__device__ __forceinline__ R load_s(const S* p) { return static_cast<R>(*p); }
+template <>
+__device__ __forceinline__ float load_s<float, __nv_bfloat16>(const __nv_bfloat16* p)
+{
+    return __bfloat162float(*p);
+}
+template <class R, class S>
+__device__ __forceinline__ void store_s(S* p, R v) { *p = static_cast<S>(v); }
+template <>
+__device__ __forceinline__ void store_s<float, __nv_bfloat16>(__nv_bfloat16* p, float v)
+{
+    *p = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------------------
+// Counter-based random numbers
+// ---------------------------------------------------------------------------
+
+// Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC'11).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Box-Muller on a pair of 32-bit words; uniforms (x + 1/2) 2^-32 lie in (0, 1].
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1)
+{
+    const float u0 = fmaf(__uint2float_rn(a), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float u1 = fmaf(__uint2float_rn(b), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
+    const float r = sqrtf(-2.0f * logf(u0));
+    float s, c;
+    sincospif(2.0f * u1, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, double& z1)
+{
+    const double u0 = ((double)a + 0.5) * 2.3283064365386963e-10;
+    const double u1 = ((double)b + 0.5) * 2.3283064365386963e-10;
+    const double r = sqrt(-2.0 * log(u0));
+    double s, c;
+    sincospi(2.0 * u1, &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// Four standard normals from the call (site, step, call | tag << 8, replica).
+template <class R>
+__device__ __forceinline__ void normals4(uint32_t k0, uint32_t k1, uint32_t site, uint32_t step,
+                                         uint32_t call_tag, uint32_t replica, R z[4])
+{
+    const uint4 r = philox4x32_10(make_uint4(site, step, call_tag, replica), k0, k1);
+    box_muller(r.x, r.y, z[0], z[1]);
+    box_muller(r.z, r.w, z[2], z[3]);
+}
+
+// ---------------------------------------------------------------------------
+// Collision parameters (per launch, in the kernel's parameter bank)
+// ---------------------------------------------------------------------------
+template <class R>
+struct Coll {
+    R rho0;
+    R om_b, om_s, om_g;   // lattice relaxation rates lambda^LB of bulk, shear, ghost modes
+    R h_b, h_s;           // 1 - omega/2 of the bulk and shear modes (forcing prefactor)
+    R ns[16];             // noise scale of non-conserved mode k: sqrt(kT w (2-w) N_a / cs^2) / N_a
+    R sqrt_rho0;
+    int noise;            // kT > 0
+    int noise_local;      // local rho (1) or rho0 (0) in the noise variance
+    uint32_t k0, k1;      // Philox key
+    uint32_t step, replica;
+};
+
+// ---------------------------------------------------------------------------
+// D2Q9 (App. B).  Velocity order: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
+// (-1,-1) (1,-1).  Pairs (c, -c): (1,3) (2,4) (5,7) (8,6).
+// Modes: rho, jx, jy, e = 3c^2-2, pww = cx^2-cy^2, pxy = cxcy,
+// qx = (3c^2-4)cx, qy = (3c^2-4)cy, eps = 9c^4-15c^2+2;
+// N = 1, 1/3, 1/3, 4, 4/9, 1/9, 2/3, 2/3, 16.
+// ---------------------------------------------------------------------------
+struct D2Q9 {
+    static constexpr int Q = 9, D = 2, NNC = 6, NCALL = 2, NCALL_ALL = 3;
+
+    // All nine moments of deviations g (m[0] = sum g).
+    template <class R>
+    __device__ __forceinline__ static void moments(const R g[9], R m[9])
+    {
+        const R s1 = g[1] + g[3], d1 = g[1] - g[3];
+        const R s2 = g[2] + g[4], d2 = g[2] - g[4];
+        const R s3 = g[5] + g[7], d3 = g[5] - g[7];
+        const R s4 = g[8] + g[6], d4 = g[8] - g[6];
+        const R sa = s1 + s2, sd = s3 + s4;
+        m[0] = g[0] + sa + sd;
+        m[1] = d1 + d3 + d4;
+        m[2] = d2 + d3 - d4;
+        m[3] = sa + R(4) * sd - R(2) * g[0];
+        m[4] = s1 - s2;
+        m[5] = s3 - s4;
+        m[6] = R(2) * (d3 + d4) - d1;
+        m[7] = R(2) * (d3 - d4) - d2;
+        m[8] = R(2) * g[0] - R(4) * sa + R(8) * sd;
+    }
+
+    // g_i += w_i sum_a T_ai D_a for the modes a >= 1 (D_a = increment / N_a).
+    template <class R>
+    __device__ __forceinline__ static void add_back(const R Dm[9], R g[9])
+    {
+        const R De = Dm[3], Dw = Dm[4], Dxy = Dm[5], Dqx = Dm[6], Dqy = Dm[7], Dep = Dm[8];
+        g[0] += R(4.0 / 9.0) * (R(2) * (Dep - De));
+        const R E1 = De + Dw - R(4) * Dep, O1 = Dm[1] - Dqx;
+        const R E2 = De - Dw - R(4) * Dep, O2 = Dm[2] - Dqy;
+        const R E3 = R(4) * De + Dxy + R(8) * Dep, O3 = Dm[1] + Dm[2] + R(2) * (Dqx + Dqy);
+        const R E4 = R(4) * De - Dxy + R(8) * Dep, O4 = Dm[1] - Dm[2] + R(2) * (Dqx - Dqy);
+        g[1] += R(1.0 / 9.0) * (E1 + O1);
+        g[3] += R(1.0 / 9.0) * (E1 - O1);
+        g[2] += R(1.0 / 9.0) * (E2 + O2);
+        g[4] += R(1.0 / 9.0) * (E2 - O2);
+        g[5] += R(1.0 / 36.0) * (E3 + O3);
+        g[7] += R(1.0 / 36.0) * (E3 - O3);
+        g[8] += R(1.0 / 36.0) * (E4 + O4);
+        g[6] += R(1.0 / 36.0) * (E4 - O4);
+    }
+
+    // Populations w_i sum_a T_ai D_a of all modes (D_0 included), into g.
+    template <class R>
+    __device__ __forceinline__ static void from_moments(const R Dm[9], R g[9])
+    {
+        for (int i = 0; i < 9; ++i) g[i] = R(0);
+        add_back(Dm, g);
+        g[0] += R(4.0 / 9.0) * Dm[0];
+        for (int i = 1; i < 5; ++i) g[i] += R(1.0 / 9.0) * Dm[0];
+        for (int i = 5; i < 9; ++i) g[i] += R(1.0 / 36.0) * Dm[0];
+    }
+
+    __host__ __device__ static constexpr double N(int a)
+    {
+        return a == 0 ? 1.0 : a < 3 ? 1.0 / 3 : a == 3 ? 4.0 : a == 4 ? 4.0 / 9 : a == 5 ? 1.0 / 9 : a < 8 ? 2.0 / 3 : 16.0;
+    }
+
+    // Moments of f^eq(rho, u) - w rho0 (Eq. (feq); m^eq column of Table I).
+    template <class R>
+    __device__ __forceinline__ static void eq_moments(R drho, R rho, R ux, R uy, R, R m[9])
+    {
+        m[0] = drho;
+        m[1] = rho * ux;
+        m[2] = rho * uy;
+        m[3] = R(3) * rho * (ux * ux + uy * uy);
+        m[4] = rho * (ux * ux - uy * uy);
+        m[5] = rho * ux * uy;
+        m[6] = m[7] = m[8] = R(0);
+    }
+
+    // Equilibrium (Eq. (feq)) and forcing (Guo form) moments of the stress modes.
+    template <class R>
+    __device__ __forceinline__ static void collide(R g[9], R Fx, R Fy, const Coll<R>& P, uint32_t site)
+    {
+        R m[9];
+        moments(g, m);
+        const R rho = P.rho0 + m[0];
+        const R ir = R(1) / rho;
+        const R ux = (m[1] + R(0.5) * Fx) * ir, uy = (m[2] + R(0.5) * Fy) * ir;
+        const R uxx = ux * ux, uyy = uy * uy;
+        const R eq_e = R(3) * rho * (uxx + uyy);
+        const R eq_w = rho * (uxx - uyy);
+        const R eq_xy = rho * ux * uy;
+        const R F_e = R(6) * (ux * Fx + uy * Fy);
+        const R F_w = R(2) * (ux * Fx - uy * Fy);
+        const R F_xy = ux * Fy + uy * Fx;
+        R Dm[9];
+        Dm[0] = R(0);
+        Dm[1] = R(3) * Fx;
+        Dm[2] = R(3) * Fy;
+        Dm[3] = R(0.25) * (P.h_b * F_e - P.om_b * (m[3] - eq_e));
+        Dm[4] = R(2.25) * (P.h_s * F_w - P.om_s * (m[4] - eq_w));
+        Dm[5] = R(9) * (P.h_s * F_xy - P.om_s * (m[5] - eq_xy));
+        Dm[6] = R(-1.5) * P.om_g * m[6];
+        Dm[7] = R(-1.5) * P.om_g * m[7];
+        Dm[8] = R(-1.0 / 16.0) * P.om_g * m[8];
+        if (P.noise) {
+            const R sr = P.noise_local ? sqrt(rho) : P.sqrt_rho0;
+            R z[8];
+            normals4(P.k0, P.k1, site, P.step, 0u, P.replica, z);
+            normals4(P.k0, P.k1, site, P.step, 1u, P.replica, z + 4);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) Dm[3 + k] += P.ns[k] * sr * z[k];
+        }
+        add_back(Dm, g);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// D3Q19.  Velocity order: 0 rest; 1,2 = +-x; 3,4 = +-y; 5,6 = +-z;
+// 7 (1,1,0) 8 (-1,-1,0) 9 (1,-1,0) 10 (-1,1,0) 11 (1,0,1) 12 (-1,0,-1)
+// 13 (1,0,-1) 14 (-1,0,1) 15 (0,1,1) 16 (0,-1,-1) 17 (0,1,-1) 18 (0,-1,1).
+// Pair p = 1..9 joins velocities 2p-1 and 2p (c and -c).
+// Modes (weighted Gram-Schmidt basis) and norms N_a:
+//  0 1 (1); 1-3 cx, cy, cz (1/3); 4 c^2-1 (2/3); 5 3cx^2-c^2 (4/3);
+//  6 cy^2-cz^2 (4/9); 7-9 cxcy, cycz, czcx (1/9); 10-12 (c^2-5/3)c_a (2/27);
+//  13 (cy^2-cz^2)cx, 14 (cz^2-cx^2)cy, 15 (cx^2-cy^2)cz (2/9);
+//  16 c^4-2c^2+1/3 (2/9); 17 (c^2-3/2)(3cx^2-c^2) (1/3); 18 (c^2-3/2)(cy^2-cz^2) (1/9).
+// Weights 1/3, 1/18 (axis), 1/36 (edge).
+// ---------------------------------------------------------------------------
+struct D3Q19 {
+    static constexpr int Q = 19, D = 3, NNC = 15, NCALL = 4, NCALL_ALL = 5;
+
+    template <class R>
+    __device__ __forceinline__ static void moments(const R g[19], R m[19])
+    {
+        const R s1 = g[1] + g[2], d1 = g[1] - g[2];
+        const R s2 = g[3] + g[4], d2 = g[3] - g[4];
+        const R s3 = g[5] + g[6], d3 = g[5] - g[6];
+        const R s4 = g[7] + g[8], d4 = g[7] - g[8];
+        const R s5 = g[9] + g[10], d5 = g[9] - g[10];
+        const R s6 = g[11] + g[12], d6 = g[11] - g[12];
+        const R s7 = g[13] + g[14], d7 = g[13] - g[14];
+        const R s8 = g[15] + g[16], d8 = g[15] - g[16];
+        const R s9 = g[17] + g[18], d9 = g[17] - g[18];
+        const R sa = s1 + s2 + s3;               // axis pairs
+        const R sxy = s4 + s5, sxz = s6 + s7, syz = s8 + s9;
+        const R se = sxy + sxz + syz;            // edge pairs
+        m[0] = g[0] + sa + se;
+        m[1] = d1 + d4 + d5 + d6 + d7;
+        m[2] = d2 + d4 - d5 + d8 + d9;
+        m[3] = d3 + d6 - d7 + d8 - d9;
+        m[4] = se - g[0];
+        m[5] = R(2) * s1 - s2 - s3 + sxy + sxz - R(2) * syz;
+        m[6] = s2 - s3 + sxy - sxz;
+        m[7] = s4 - s5;
+        m[8] = s8 - s9;
+        m[9] = s6 - s7;
+        m[10] = R(1.0 / 3.0) * (d4 + d5 + d6 + d7 - R(2) * d1);
+        m[11] = R(1.0 / 3.0) * (d4 - d5 + d8 + d9 - R(2) * d2);
+        m[12] = R(1.0 / 3.0) * (d6 - d7 + d8 - d9 - R(2) * d3);
+        m[13] = d4 + d5 - d6 - d7;
+        m[14] = d5 - d4 + d8 + d9;
+        m[15] = d6 - d7 - d8 + d9;
+        m[16] = R(1.0 / 3.0) * (g[0] + se - R(2) * sa);
+        m[17] = R(0.5) * (s2 + s3 + sxy + sxz) - s1 - syz;
+        m[18] = R(0.5) * (s3 - s2 + sxy - sxz);
+    }
+
+    // g_i += w_i sum_a T_ai D_a over the modes a >= 1.
+    template <class R>
+    __device__ __forceinline__ static void add_back(const R Dm[19], R g[19])
+    {
+        const R De = Dm[4], D5 = Dm[5], D6 = Dm[6], D7 = Dm[7], D8 = Dm[8], D9 = Dm[9];
+        const R D10 = Dm[10], D11 = Dm[11], D12 = Dm[12], D13 = Dm[13], D14 = Dm[14], D15 = Dm[15];
+        const R D16 = Dm[16], D17 = Dm[17], D18 = Dm[18];
+        const R Jx = Dm[1], Jy = Dm[2], Jz = Dm[3];
+        const R t16 = R(1.0 / 3.0) * D16, h17 = R(0.5) * D17, h18 = R(0.5) * D18;
+        const R a10 = R(1.0 / 3.0) * D10, a11 = R(1.0 / 3.0) * D11, a12 = R(1.0 / 3.0) * D12;
+        // rest particle: e = -1, c^4-2c^2+1/3 = 1/3
+        g[0] += R(1.0 / 3.0) * (t16 - De);
+        // axis pairs: e = 0, c^4-term = -2/3
+        const R Ea = R(-2) * t16;
+        const R E1 = Ea + R(2) * D5 - D17, O1 = Jx - R(2) * a10;
+        const R E2 = Ea - D5 + D6 + h17 - h18, O2 = Jy - R(2) * a11;
+        const R E3 = Ea - D5 - D6 + h17 + h18, O3 = Jz - R(2) * a12;
+        // edge pairs: e = 1, c^4-term = 1/3
+        const R Ee = De + t16;
+        const R Exy = Ee + D5 + D6 + h17 + h18;
+        const R E4 = Exy + D7, O4 = Jx + Jy + a10 + a11 + D13 - D14;
+        const R E5 = Exy - D7, O5 = Jx - Jy + a10 - a11 + D13 + D14;
+        const R Exz = Ee + D5 - D6 + h17 - h18;
+        const R E6 = Exz + D9, O6 = Jx + Jz + a10 + a12 - D13 + D15;
+        const R E7 = Exz - D9, O7 = Jx - Jz + a10 - a12 - D13 - D15;
+        const R Eyz = Ee - R(2) * D5 - D17;
+        const R E8 = Eyz + D8, O8 = Jy + Jz + a11 + a12 + D14 - D15;
+        const R E9 = Eyz - D8, O9 = Jy - Jz + a11 - a12 + D14 + D15;
+        constexpr double wa = 1.0 / 18.0, we = 1.0 / 36.0;
+        g[1] += R(wa) * (E1 + O1);
+        g[2] += R(wa) * (E1 - O1);
+        g[3] += R(wa) * (E2 + O2);
+        g[4] += R(wa) * (E2 - O2);
+        g[5] += R(wa) * (E3 + O3);
+        g[6] += R(wa) * (E3 - O3);
+        g[7] += R(we) * (E4 + O4);
+        g[8] += R(we) * (E4 - O4);
+        g[9] += R(we) * (E5 + O5);
+        g[10] += R(we) * (E5 - O5);
+        g[11] += R(we) * (E6 + O6);
+        g[12] += R(we) * (E6 - O6);
+        g[13] += R(we) * (E7 + O7);
+        g[14] += R(we) * (E7 - O7);
+        g[15] += R(we) * (E8 + O8);
+        g[16] += R(we) * (E8 - O8);
+        g[17] += R(we) * (E9 + O9);
+        g[18] += R(we) * (E9 - O9);
+    }
+
+    template <class R>
+    __device__ __forceinline__ static void from_moments(const R Dm[19], R g[19])
+    {
+        for (int i = 0; i < 19; ++i) g[i] = R(0);
+        add_back(Dm, g);
+        g[0] += R(1.0 / 3.0) * Dm[0];
+        for (int i = 1; i < 7; ++i) g[i] += R(1.0 / 18.0) * Dm[0];
+        for (int i = 7; i < 19; ++i) g[i] += R(1.0 / 36.0) * Dm[0];
+    }
+
+    __host__ __device__ static constexpr double N(int a)
+    {
+        return a == 0 ? 1.0 : a < 4 ? 1.0 / 3 : a == 4 ? 2.0 / 3 : a == 5 ? 4.0 / 3 : a == 6 ? 4.0 / 9
+             : a < 10 ? 1.0 / 9 : a < 13 ? 2.0 / 27 : a < 17 ? 2.0 / 9 : a == 17 ? 1.0 / 3 : 1.0 / 9;
+    }
+
+    // Moments of f^eq(rho, u) - w rho0 (Eq. (feq)); ghosts vanish.
+    template <class R>
+    __device__ __forceinline__ static void eq_moments(R drho, R rho, R ux, R uy, R uz, R m[19])
+    {
+        const R uu = ux * ux + uy * uy + uz * uz;
+        m[0] = drho;
+        m[1] = rho * ux;
+        m[2] = rho * uy;
+        m[3] = rho * uz;
+        m[4] = rho * uu;
+        m[5] = rho * (R(3) * ux * ux - uu);
+        m[6] = rho * (uy * uy - uz * uz);
+        m[7] = rho * ux * uy;
+        m[8] = rho * uy * uz;
+        m[9] = rho * uz * ux;
+        for (int a = 10; a < 19; ++a) m[a] = R(0);
+    }
+
+    template <class R>
+    __device__ __forceinline__ static void collide(R g[19], R Fx, R Fy, R Fz, const Coll<R>& P, uint32_t site)
+    {
+        R m[19];
+        moments(g, m);
+        const R rho = P.rho0 + m[0];
+        const R ir = R(1) / rho;
+        const R ux = (m[1] + R(0.5) * Fx) * ir;
+        const R uy = (m[2] + R(0.5) * Fy) * ir;
+        const R uz = (m[3] + R(0.5) * Fz) * ir;
+        const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, uu = uxx + uyy + uzz;
+        const R uFx = ux * Fx, uFy = uy * Fy, uFz = uz * Fz, uF = uFx + uFy + uFz;
+        R Dm[19];
+        Dm[0] = R(0);
+        Dm[1] = R(3) * Fx;
+        Dm[2] = R(3) * Fy;
+        Dm[3] = R(3) * Fz;
+        // bulk: m^eq = rho u^2, m^F = 2 u.F
+        Dm[4] = R(1.5) * (P.h_b * R(2) * uF - P.om_b * (m[4] - rho * uu));
+        // shear: m^eq = rho(3ux^2-u^2), rho(uy^2-uz^2), rho ux uy, rho uy uz, rho uz ux
+        Dm[5] = R(0.75) * (P.h_s * R(2) * (R(3) * uFx - uF) - P.om_s * (m[5] - rho * (R(3) * uxx - uu)));
+        Dm[6] = R(2.25) * (P.h_s * R(2) * (uFy - uFz) - P.om_s * (m[6] - rho * (uyy - uzz)));
+        Dm[7] = R(9) * (P.h_s * (ux * Fy + uy * Fx) - P.om_s * (m[7] - rho * ux * uy));
+        Dm[8] = R(9) * (P.h_s * (uy * Fz + uz * Fy) - P.om_s * (m[8] - rho * uy * uz));
+        Dm[9] = R(9) * (P.h_s * (uz * Fx + ux * Fz) - P.om_s * (m[9] - rho * uz * ux));
+        // ghosts relax to 0
+        const R og = P.om_g;
+        Dm[10] = R(-13.5) * og * m[10];
+        Dm[11] = R(-13.5) * og * m[11];
+        Dm[12] = R(-13.5) * og * m[12];
+        Dm[13] = R(-4.5) * og * m[13];
+        Dm[14] = R(-4.5) * og * m[14];
+        Dm[15] = R(-4.5) * og * m[15];
+        Dm[16] = R(-4.5) * og * m[16];
+        Dm[17] = R(-3) * og * m[17];
+        Dm[18] = R(-9) * og * m[18];
+        if (P.noise) {
+            const R sr = P.noise_local ? sqrt(rho) : P.sqrt_rho0;
+            R z[16];
+            normals4(P.k0, P.k1, site, P.step, 0u, P.replica, z);
+            normals4(P.k0, P.k1, site, P.step, 1u, P.replica, z + 4);
+            normals4(P.k0, P.k1, site, P.step, 2u, P.replica, z + 8);
+            normals4(P.k0, P.k1, site, P.step, 3u, P.replica, z + 12);
+#pragma unroll
+            for (int k = 0; k < 15; ++k) Dm[4 + k] += P.ns[k] * sr * z[k];
+        }
+        add_back(Dm, g);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Geometry helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrap_once(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+__device__ __forceinline__ int wrap_any(int a, int n)
+{
+    while (a < 0) a += n;
+    while (a >= n) a -= n;
+    return a;
+}
+
+}  // namespace flb

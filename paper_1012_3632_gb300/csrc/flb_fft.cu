@@ -1,0 +1,264 @@
+// flb_fft.cu -- precision-independent kernels: deterministic column sums for
+// the reductions, a mixed-radix (2, 3, 4, 5) Stockham FFT in double precision
+// for the structure factors, and the power spectrum accumulation.
+//
+// Structure factor of mode a (Sec. IV, Eq. (g-correl); Sec. VI equilibration
+// ratios): S_a(k) = |sum_r dm_a(r) exp(-i k.r)|^2 / V, accumulated in double.
+#include <cmath>
+
+#include "flb_internal.h"
+
+namespace flb {
+
+// ---------------------------------------------------------------------------
+// Column sums (one block per column, fixed order: deterministic)
+// ---------------------------------------------------------------------------
+__global__ void k_sum_columns(const double* __restrict__ partials, int nrows, int ncol, double* __restrict__ out)
+{
+    __shared__ double sh[256];
+    const int c = blockIdx.x;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) acc += partials[(long)r * ncol + c];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[c] = sh[0];
+}
+
+cudaError_t sum_columns(const double* partials, int nrows, int ncol, double* out, cudaStream_t s)
+{
+    k_sum_columns<<<ncol, 256, 0, s>>>(partials, nrows, ncol, out);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// FFT
+// ---------------------------------------------------------------------------
+struct FftPlan {
+    int L;
+    int nrad;
+    int rad[32];
+};
+
+// Factor L into radices 4, 2, 3, 5; false if another prime remains.
+static bool make_plan(int L, FftPlan& p)
+{
+    p.L = L;
+    p.nrad = 0;
+    int n = L;
+    while (n % 4 == 0) {
+        p.rad[p.nrad++] = 4;
+        n /= 4;
+    }
+    while (n % 2 == 0) {
+        p.rad[p.nrad++] = 2;
+        n /= 2;
+    }
+    while (n % 3 == 0) {
+        p.rad[p.nrad++] = 3;
+        n /= 3;
+    }
+    while (n % 5 == 0) {
+        p.rad[p.nrad++] = 5;
+        n /= 5;
+    }
+    return n == 1 && p.nrad <= 32;
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// Line geometry: line (i0, i1) starts at i0*s_in + i1*s_out, elements es apart.
+struct LineGeom {
+    int L;
+    long es, s_in, s_out;
+    int n_in;
+};
+
+// One Stockham pass (Govindaraju et al., SC'08 formulation): butterfly j of
+// radix R with Ns = product of the radices already applied reads in[j + r L/R],
+// twiddles by exp(-2 pi i r (j mod Ns) / (Ns R)), applies the R-point DFT and
+// writes out[(j / Ns) Ns R + (j mod Ns) + r Ns].
+__device__ __forceinline__ void butterfly(const double2* __restrict__ in, double2* __restrict__ out, int L, int R,
+                                          int Ns, int j)
+{
+    const int stride = L / R;
+    const int k = j % Ns;
+    double2 v[5];
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
+    if (Ns > 1) {
+        double s, c;
+        sincospi(-2.0 * (double)k / (double)(Ns * R), &s, &c);
+        const double2 w1 = make_double2(c, s);
+        double2 w = w1;
+        for (int r = 1; r < R; ++r) {
+            v[r] = cmul(v[r], w);
+            w = cmul(w, w1);
+        }
+    }
+    double2 y[5];
+    if (R == 2) {
+        y[0] = cadd(v[0], v[1]);
+        y[1] = csub(v[0], v[1]);
+    } else if (R == 4) {
+        const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        const double2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        y[0] = cadd(a, c);
+        y[2] = csub(a, c);
+        y[1] = make_double2(b.x + d.y, b.y - d.x);  // b - i d
+        y[3] = make_double2(b.x - d.y, b.y + d.x);  // b + i d
+    } else if (R == 3) {
+        const double h = 0.86602540378443864676;  // sqrt(3)/2
+        const double2 t = cadd(v[1], v[2]), u = csub(v[1], v[2]);
+        y[0] = cadd(v[0], t);
+        const double2 m = make_double2(v[0].x - 0.5 * t.x, v[0].y - 0.5 * t.y);
+        y[1] = make_double2(m.x + h * u.y, m.y - h * u.x);  // m - i h u
+        y[2] = make_double2(m.x - h * u.y, m.y + h * u.x);  // m + i h u
+    } else {  // R == 5: direct 5-point DFT
+        for (int q = 0; q < 5; ++q) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int r = 0; r < 5; ++r) {
+                double s, c;
+                sincospi(-2.0 * (double)((q * r) % 5) / 5.0, &s, &c);
+                acc = cadd(acc, cmul(v[r], make_double2(c, s)));
+            }
+            y[q] = acc;
+        }
+    }
+    const int base = (j / Ns) * Ns * R + k;
+    for (int r = 0; r < R; ++r) out[base + r * Ns] = y[r];
+}
+
+__global__ void k_fft_lines(double2* __restrict__ data, const FftPlan plan, const LineGeom g, int B)
+{
+    extern __shared__ double2 sm[];
+    const int L = g.L;
+    double2* b0 = sm;
+    double2* b1 = sm + (long)B * L;
+    const int i0 = blockIdx.x * B;
+    const long o1 = (long)blockIdx.y * g.s_out;
+    const int nl = min(B, g.n_in - i0);
+    const int tot = nl * L;
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        int l, j;
+        if (g.es == 1) {
+            l = e / L;
+            j = e % L;
+        } else {
+            l = e % nl;
+            j = e / nl;
+        }
+        b0[l * L + j] = data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es];
+    }
+    __syncthreads();
+    int Ns = 1;
+    double2* cur = b0;
+    double2* nxt = b1;
+    for (int p = 0; p < plan.nrad; ++p) {
+        const int R = plan.rad[p];
+        const int per = L / R;
+        for (int t = threadIdx.x; t < nl * per; t += blockDim.x) {
+            const int l = t / per, j = t % per;
+            butterfly(cur + l * L, nxt + l * L, L, R, Ns, j);
+        }
+        __syncthreads();
+        Ns *= R;
+        double2* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+    }
+    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+        int l, j;
+        if (g.es == 1) {
+            l = e / L;
+            j = e % L;
+        } else {
+            l = e % nl;
+            j = e / nl;
+        }
+        data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es] = cur[l * L + j];
+    }
+}
+
+// Direct DFT for lengths with prime factors above 5 (small test lattices).
+__global__ void k_dft_lines_naive(const double2* __restrict__ in, double2* __restrict__ out, const LineGeom g,
+                                  int n_out)
+{
+    const long tot = (long)g.n_in * n_out * g.L;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % g.L);
+        const long line = e / g.L;
+        const int i0 = (int)(line % g.n_in);
+        const long i1 = line / g.n_in;
+        const long base = i0 * g.s_in + i1 * g.s_out;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int j = 0; j < g.L; ++j) {
+            const int m = (int)(((long)j * k) % g.L);
+            double s, c;
+            sincospi(-2.0 * (double)m / (double)g.L, &s, &c);
+            acc = cadd(acc, cmul(in[base + j * g.es], make_double2(c, s)));
+        }
+        out[base + k * g.es] = acc;
+    }
+}
+
+static cudaError_t fft_axis(double2* data, double2* scratch, int L, long es, long s_in, int n_in, long s_out,
+                            int n_out, long V, cudaStream_t s)
+{
+    if (L == 1) return cudaSuccess;
+    FftPlan plan;
+    const LineGeom g{L, es, s_in, s_out, n_in};
+    if (L <= 4096 && make_plan(L, plan)) {
+        const int B = L >= 2048 ? 1 : (2048 / L < 16 ? 2048 / L : 16);
+        const size_t smem = 2ull * B * L * sizeof(double2);
+        cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const dim3 grid((n_in + B - 1) / B, n_out);
+        k_fft_lines<<<grid, 256, smem, s>>>(data, plan, g, B);
+        return cudaGetLastError();
+    }
+    k_dft_lines_naive<<<1024, 256, 0, s>>>(data, scratch, g, n_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return cudaMemcpyAsync(data, scratch, V * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+}
+
+cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s)
+{
+    const long V = (long)X * Y * Z;
+    cudaError_t e;
+    // x lines: inner index y, outer z
+    if ((e = fft_axis(data, scratch, X, 1, X, Y, (long)X * Y, Z, V, s)) != cudaSuccess) return e;
+    // y lines: inner x, outer z
+    if ((e = fft_axis(data, scratch, Y, X, 1, X, (long)X * Y, Z, V, s)) != cudaSuccess) return e;
+    // z lines: inner x, outer y
+    return fft_axis(data, scratch, Z, (long)X * Y, 1, X, X, Y, V, s);
+}
+
+__global__ void k_power(const double2* __restrict__ d, long V, double* __restrict__ acc, double* __restrict__ out)
+{
+    for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < V; s += (long)gridDim.x * blockDim.x) {
+        const double p = (s == 0) ? 0.0 : (d[s].x * d[s].x + d[s].y * d[s].y) / (double)V;
+        if (acc)
+            acc[s] += p;
+        else
+            out[s] = p;
+    }
+}
+
+cudaError_t power_spectrum(const double2* data, long V, double* acc, double* out, cudaStream_t s)
+{
+    long nb = (V + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_power<<<(unsigned)nb, 256, 0, s>>>(data, V, acc, out);
+    return cudaGetLastError();
+}
+
+}  // namespace flb

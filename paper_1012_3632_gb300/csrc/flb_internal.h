@@ -1,0 +1,63 @@
+// flb_internal.h -- host-side interface between the C ABI (flb_api.cu) and the
+// precision-specific kernel instantiations (flb_fp64.cu, flb_fp32.cu,
+// flb_bf16.cu) and the precision-independent kernels (flb_fft.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace flb {
+
+// Model parameters in double; each instantiation converts to its compute type.
+struct HostModel {
+    int Q, D, X, Y, Z;
+    long V;
+    double rho0;
+    double om_s, om_b, om_g, kT;
+    int nonideal;
+    double A, B, rho_c, kappa;
+    uint64_t seed;
+    uint32_t replica;
+    int noise_local;
+};
+
+// Kernels whose code depends on the compute/storage type.  Pointers are device
+// pointers; `pop` buffers hold Q*V elements of the storage type, `field`
+// buffers V (or 3V) elements of the compute type.
+struct PrecOps {
+    int elem_size;    // bytes per stored population
+    int real_size;    // bytes per compute-type scalar (density/force fields)
+    cudaError_t (*density)(const HostModel&, const void* pop, void* drho, cudaStream_t);
+    cudaError_t (*step)(const HostModel&, uint64_t step, const void* src, void* dst, const void* drho,
+                        cudaStream_t);
+    cudaError_t (*init)(const HostModel&, void* dst, const double* rho, const double* u, int thermal,
+                        cudaStream_t);
+    cudaError_t (*get_pop)(const HostModel&, const void* src, double* out, cudaStream_t);
+    cudaError_t (*set_pop)(const HostModel&, const double* in, void* dst, cudaStream_t);
+    // which: 0 rho, 1 u (needs F or NULL for the ideal gas), 2 modes
+    cudaError_t (*moments)(const HostModel&, const void* src, double* out, int which, const void* F,
+                           cudaStream_t);
+    cudaError_t (*mu_force)(const HostModel&, const void* drho, void* mu, void* F, cudaStream_t);
+    // per-block partial sums; returns the number of partial rows written
+    cudaError_t (*mode_partials)(const HostModel&, const void* src, double* partials, int* nrows,
+                                 cudaStream_t);
+    cudaError_t (*cons_partials)(const HostModel&, const void* src, double* partials, int* nrows,
+                                 cudaStream_t);
+    cudaError_t (*mode_field)(const HostModel&, const void* src, int mode, double2* out, cudaStream_t);
+    int (*partial_rows_max)(const HostModel&);
+};
+
+const PrecOps& ops_fp64();
+const PrecOps& ops_fp32();
+const PrecOps& ops_bf16();
+
+// Deterministic column sums: out[c] = sum_r partials[r*ncol + c] (flb_fft.cu).
+cudaError_t sum_columns(const double* partials, int nrows, int ncol, double* out, cudaStream_t s);
+
+// In-place forward DFT along every axis of length > 1 of a complex X*Y*Z field.
+cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s);
+
+// p = |data|^2 / V with p(0) = 0; accumulate: acc += p, else out = p.
+cudaError_t power_spectrum(const double2* data, long V, double* acc, double* out, cudaStream_t s);
+
+}  // namespace flb

@@ -1,0 +1,286 @@
+"""GPU <-> oracle parity through the C ABI (same seeds, same inputs).
+
+Tolerances (on max |df| of the pre-collision populations):
+  FP64 path   1e-12 (both sides double; only rounding order differs)
+  FP32 path   2e-5 * rho0 after 100 steps (float deviation storage)
+  BF16 path   bfloat16 keeps 8 mantissa bits of deviations |g| <~ 0.02:
+              ~4e-5 rounding per step; 2e-3 after 20 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_3632_gb300 import BF16, D2Q9, D3Q19, FP32, FP64, MODE_VAR, MODES, RHO, U, Context, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 2e-5, "bf16": 2e-3}
+FE = dict(A=-0.01, B=0.1, rho_c=1.0, kappa=0.02)
+
+
+def _pair(Q, dims, prec, fe=None, **kw):
+    ctx = Context(Q, dims, precision=prec, free_energy=fe, **kw)
+    p = oracle.Params(Q=Q, dims=dims, nonideal=fe is not None, **(fe or {}), **kw)
+    return ctx, p
+
+
+def _run_both(Q, dims, prec, steps, fe=None, rho=None, u=None, thermal=False, **kw):
+    ctx, p = _pair(Q, dims, prec, fe, **kw)
+    with ctx:
+        ctx.init(rho=rho, u=u, thermal=thermal)
+        ctx.step(steps)
+        got = ctx.get_populations()
+    want = oracle.run(p, oracle.init(p, rho=rho, u=u, thermal=thermal), 0, steps)
+    return got, want
+
+
+def test_config0_d2q9_fp64_100_steps():
+    """D2Q9 ideal gas 32x32, FP64, rho0 = 1, kT = 1e-4, all rates 1, f = w rho0, seed 1."""
+    got, want = _run_both(9, (32, 32, 1), "fp64", 100, kT=1e-4, omega_shear=1.0, omega_bulk=1.0,
+                          omega_ghost=1.0, seed=1)
+    assert np.abs(got - want).max() <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("Q,dims", [(9, (17, 13, 1)), (19, (12, 10, 9)), (19, (1, 1, 1)), (19, (2, 3, 5)),
+                                    (9, (1, 1, 1)), (19, (33, 5, 3))])
+def test_fp64_ideal_ragged(Q, dims):
+    D = 2 if Q == 9 else 3
+    u = inputs.random_velocity(dims, D, amp=0.02, seed=2)
+    got, want = _run_both(Q, dims, "fp64", 60, u=u, thermal=True, kT=1e-4, omega_shear=1.3,
+                          omega_bulk=0.8, omega_ghost=1.55, seed=7)
+    assert np.abs(got - want).max() <= TOL["fp64"]
+
+
+@pytest.mark.parametrize("Q,dims", [(9, (24, 19, 1)), (19, (12, 10, 9)), (19, (35, 6, 5)), (19, (3, 2, 2))])
+def test_fp64_nonideal(Q, dims):
+    rho = inputs.uniform_density(dims, seed=4)
+    got, want = _run_both(Q, dims, "fp64", 60, fe=FE, rho=rho, thermal=True, kT=1e-6, omega_shear=1.1,
+                          omega_bulk=1.0, omega_ghost=1.2, seed=9)
+    assert np.abs(got - want).max() <= TOL["fp64"]
+
+
+def test_fp64_random_state_noise_rho0():
+    """A generic non-equilibrium start, noise with the reference density (noise_rho_local = 0)."""
+    dims = (9, 8, 7)
+    f0 = inputs.random_populations(19, dims, seed=3)
+    kw = dict(kT=1e-4, omega_shear=0.7, omega_bulk=1.6, omega_ghost=1.9, seed=2 ** 40 + 3, replica=5)
+    ctx = Context(19, dims, precision="fp64", noise_rho_local=False, **kw)
+    p = oracle.Params(Q=19, dims=dims, noise_rho_local=False, **kw)
+    with ctx:
+        ctx.set_populations(f0)
+        assert np.abs(ctx.get_populations() - f0).max() < 1e-15
+        ctx.step_count = 1000
+        ctx.step(30)
+        got = ctx.get_populations()
+    want = oracle.run(p, f0, 1000, 30)
+    assert np.abs(got - want).max() <= TOL["fp64"]
+
+
+def test_fp32_config1_like_100_steps():
+    """D3Q19 ideal, FP32 deviations, kT = 1e-5, rates (1.2, 1, 1), shear wave + thermal start."""
+    dims = (16, 16, 16)
+    u = inputs.shear_wave(dims, amp=1e-3)
+    got, want = _run_both(19, dims, "fp32", 100, u=u, thermal=True, kT=1e-5, omega_shear=1.2, omega_bulk=1.0,
+                          omega_ghost=1.0, seed=2)
+    assert np.abs(got - want).max() <= TOL["fp32"]
+
+
+def test_fp32_config2_like_100_steps():
+    """D3Q19 non-ideal (A=-0.01, B=0.1, rho_c=1, kappa=0.02), FP32, kT = 1e-6, rates 1."""
+    dims = (16, 14, 12)
+    rho = inputs.uniform_density(dims, seed=3)
+    got, want = _run_both(19, dims, "fp32", 100, fe=FE, rho=rho, kT=1e-6, omega_shear=1.0, omega_bulk=1.0,
+                          omega_ghost=1.0, seed=3)
+    assert np.abs(got - want).max() <= TOL["fp32"]
+
+
+def test_fp32_d2q9_nonideal():
+    dims = (40, 33, 1)
+    rho = inputs.uniform_density(dims, seed=8)
+    got, want = _run_both(9, dims, "fp32", 100, fe=FE, rho=rho, thermal=True, kT=1e-5, omega_shear=1.4,
+                          omega_bulk=0.9, omega_ghost=1.0, seed=5)
+    assert np.abs(got - want).max() <= TOL["fp32"]
+
+
+def test_bf16_storage():
+    dims = (16, 12, 10)
+    got, want = _run_both(19, dims, "bf16", 20, thermal=True, kT=1e-5, omega_shear=1.2, omega_bulk=1.0,
+                          omega_ghost=1.0, seed=4)
+    assert np.abs(got - want).max() <= TOL["bf16"]
+
+
+@pytest.mark.parametrize("Q,dims", [(19, (6, 5, 4)), (9, (7, 5, 1))])
+def test_init_parity(Q, dims):
+    D = 2 if Q == 9 else 3
+    rho = inputs.uniform_density(dims, amp=0.05, seed=1)
+    u = inputs.random_velocity(dims, D, seed=1)
+    kw = dict(kT=1e-4, omega_shear=1.0, seed=12)
+    ctx, p = _pair(Q, dims, "fp64", **kw)
+    with ctx:
+        ctx.init(rho=rho, u=u, thermal=True)
+        got = ctx.get_populations()
+        assert ctx.step_count == 0
+    want = oracle.init(p, rho=rho, u=u, thermal=True)
+    assert np.abs(got - want).max() <= 1e-15
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("fe", [None, FE])
+def test_observables(prec, fe):
+    Q, dims = 19, (10, 9, 8)
+    rho = inputs.uniform_density(dims, seed=2)
+    kw = dict(kT=1e-5, omega_shear=1.2, seed=3)
+    ctx, p = _pair(Q, dims, prec, fe, **kw)
+    tol = 1e-13 if prec == "fp64" else 1e-6
+    with ctx:
+        ctx.init(rho=rho, thermal=True)
+        ctx.step(5)
+        f = ctx.get_populations()
+        r = ctx.moments(RHO)
+        u = ctx.moments(U)
+        m = ctx.moments(MODES)
+        cons = ctx.conservation()
+    f_or = oracle.run(p, oracle.init(p, rho=rho, thermal=True), 0, 5)
+    assert np.abs(f - f_or).max() <= TOL[prec]
+    # observables of the GPU state, recomputed by the oracle
+    assert np.abs(r - f.sum(axis=0)).max() <= tol
+    assert np.abs(u - oracle.velocity(p, f)).max() <= tol
+    assert np.abs(m - oracle.modes(p, f)).max() <= tol
+    L = oracle.lattice(Q)
+    c = L.c.astype(float)
+    assert abs(cons[0] - f.sum()) <= 1e-9
+    assert np.allclose(cons[1:], (c.T @ f).sum(axis=1), atol=1e-9)
+
+
+@pytest.mark.parametrize("dims", [(6, 5, 4), (8, 8, 8), (12, 10, 9), (7, 3, 1), (16, 1, 1)])
+def test_structure_factor(dims):
+    Q = 9 if dims[2] == 1 and dims[1] > 1 and dims[0] == 7 else 19
+    if Q == 9:
+        dims = (dims[0], dims[1], 1)
+    kw = dict(kT=1e-4, omega_shear=1.2, seed=6)
+    ctx, p = _pair(Q, dims, "fp64", **kw)
+    with ctx:
+        ctx.init(thermal=True)
+        ctx.step(3)
+        f = ctx.get_populations()
+        for mode in (0, 1, Q - 1):
+            S = ctx.structure_factor(mode)
+            want = oracle.structure_factor(p, f, mode)
+            assert np.allclose(S, want, rtol=1e-10, atol=1e-18), mode
+        # accumulation over snapshots = mean of the snapshots
+        s1 = ctx.structure_factor(0, accumulate=True)
+        ctx.step(2)
+        s2 = ctx.structure_factor(0, accumulate=False)
+        mean = ctx.structure_factor(0, accumulate=True)
+        assert ctx.snapshot_count(0) == 2
+        assert np.allclose(mean, 0.5 * (s1 + s2), rtol=1e-12, atol=1e-20)
+
+
+def test_mode_variance_accumulator():
+    Q, dims = 19, (8, 7, 6)
+    kw = dict(kT=1e-4, omega_shear=1.2, seed=6)
+    ctx, p = _pair(Q, dims, "fp64", **kw)
+    with ctx:
+        ctx.init(thermal=True)
+        v1 = ctx.moments(MODE_VAR)
+        f1 = ctx.get_populations()
+        ctx.step(4)
+        v2 = ctx.moments(MODE_VAR)
+        f2 = ctx.get_populations()
+        assert ctx.snapshot_count(-1) == 2
+    var = lambda f: oracle.modes(p, f).var(axis=1)
+    assert np.allclose(v1, var(f1), rtol=1e-10, atol=1e-20)
+    assert np.allclose(v2, 0.5 * (var(f1) + var(f2)), rtol=1e-10, atol=1e-20)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "bf16"])
+def test_checkpoint_resume_is_bitwise(tmp_path, prec):
+    Q, dims = 19, (9, 8, 7)
+    kw = dict(kT=1e-5, omega_shear=1.2, seed=8, free_energy=FE)
+    rho = inputs.uniform_density(dims, seed=6)
+    with Context(Q, dims, precision=prec, **kw) as a:
+        a.init(rho=rho, thermal=True)
+        a.step(7)
+        a.save(str(tmp_path / "c.flb"))
+        a.step(9)
+        fa = a.get_populations()
+    with Context.load(str(tmp_path / "c.flb")) as b:
+        assert b.step_count == 7
+        b.step(9)
+        fb = b.get_populations()
+    assert np.array_equal(fa, fb)
+
+
+def test_kernel_timing_counts_launches():
+    with Context(19, (32, 16, 8), precision="fp32", free_energy=FE, kT=1e-6, omega_shear=1.0) as ctx:
+        ctx.init(rho=inputs.uniform_density((32, 16, 8)))
+        ctx.kernel_timing(True)
+        ctx.step(5)
+        ms, n = ctx.kernel_times()
+        assert list(n[:2]) == [5, 5] and ms[0] > 0 and ms[1] > 0
+
+
+def test_divergence_is_reported():
+    """A NaN population (set on the host) makes the next checked step return FLB_EDIVERGED."""
+    from paper_1012_3632_gb300 import FLBError
+
+    dims = (6, 6, 6)
+    with Context(19, dims, precision="fp32", kT=1e-5, omega_shear=1.0, check_every=1) as ctx:
+        f = ctx.get_populations()
+        f[3, 17] = np.nan
+        ctx.set_populations(f)
+        with pytest.raises(FLBError) as e:
+            ctx.step(1)
+        assert e.value.code == -4
+
+
+# ---------------------------------------------------------------------------
+# Full-size workloads: sampled sites against oracle windows
+# ---------------------------------------------------------------------------
+
+def _window_check(Q, dims, prec, steps, fe, rho, u, thermal, kw, centres, tol):
+    ctx, p = _pair(Q, dims, prec, fe, **kw)
+    with ctx:
+        ctx.init(rho=rho, u=u, thermal=thermal)
+        ctx.step(steps)
+        f = ctx.get_populations()
+    D = 2 if Q == 9 else 3
+    radius = steps * (3 if fe else 1)  # light cone: streaming 1, force stencils 2 more
+    X, Y, Z = dims
+    for cen in centres:
+        h = radius + 1
+        org = tuple(c - h for c in cen)
+        win = tuple(2 * h + 1 for _ in cen)
+        if D == 2:
+            org, win = (org[0], org[1], 0), (win[0], win[1], 1)
+        gx = (np.arange(win[0]) + org[0]) % X
+        gy = (np.arange(win[1]) + org[1]) % Y
+        gz = (np.arange(win[2]) + org[2]) % Z
+        sites = (gx[None, None, :] + X * (gy[None, :, None] + Y * gz[:, None, None])).reshape(-1)
+        pw = p.with_(origin=org, window=win)
+        rw = None if rho is None else rho[sites]
+        uw = None if u is None else u[:, sites]
+        fw = oracle.run(pw, oracle.init(pw, rho=rw, u=uw, thermal=thermal), 0, steps)
+        c_local = (h, h, h if D == 3 else 0)
+        s_loc = c_local[0] + win[0] * (c_local[1] + win[1] * c_local[2])
+        s_glob = cen[0] + X * (cen[1] + Y * (cen[2] if D == 3 else 0))
+        assert np.isfinite(fw[:, s_loc]).all()
+        assert np.abs(f[:, s_glob] - fw[:, s_loc]).max() <= tol, cen
+
+
+def test_full_size_config2_sampled():
+    """256^3 non-ideal FP32 (the benchmark workload): 3 steps, 4 sampled sites."""
+    dims = (256, 256, 256)
+    rho = inputs.uniform_density(dims, seed=3)
+    kw = dict(kT=1e-6, omega_shear=1.0, omega_bulk=1.0, omega_ghost=1.0, seed=3)
+    centres = [(0, 0, 0), (255, 17, 128), (100, 255, 3), (37, 200, 255)]
+    _window_check(19, dims, "fp32", 3, FE, rho, None, False, kw, centres, TOL["fp32"])
+
+
+def test_full_size_config1_sampled():
+    """128^3 ideal FP32 with shear wave and thermal start: 5 steps, 4 sampled sites."""
+    dims = (128, 128, 128)
+    u = inputs.shear_wave(dims, amp=1e-3)
+    kw = dict(kT=1e-5, omega_shear=1.2, omega_bulk=1.0, omega_ghost=1.0, seed=2)
+    centres = [(0, 0, 0), (127, 64, 1), (5, 127, 127), (90, 33, 64)]
+    _window_check(19, dims, "fp32", 5, None, None, u, True, kw, centres, TOL["fp32"])
