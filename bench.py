@@ -37,14 +37,24 @@ WORKLOADS = {
                              "psi=A(rho-rho_c)^2/2+B(rho-rho_c)^4/4 (A=-0.01, B=0.1, rho_c=1), kappa=0.02, "
                              "F=-rho grad mu (19-point stencils), Guo forcing, kT=1e-6, omega_shear=1, "
                              "rho=1+U(-0.01,0.01)"),
+    "nonideal128": dict(lattice=19, dims=(128, 128, 128), precision="fp32", fe=FE, kT=1e-6,
+                        omega=(1.0, 1.0, 1.0), seed=3,
+                        name="D3Q19 force-based non-ideal fluid, 128^3 periodic, FP32 deviations, "
+                             "parameters of the 256^3 workload (profiling size)"),
+    "ideal256": dict(lattice=19, dims=(256, 256, 256), precision="fp32", fe=None, kT=1e-5,
+                     omega=(1.2, 1.0, 1.0), seed=2,
+                     name="D3Q19 ideal gas, 256^3 periodic, FP32 deviations, kT=1e-5, "
+                          "omega=(1.2, 1.0, 1.0), shear wave + thermal start"),
     "ideal128": dict(lattice=19, dims=(128, 128, 128), precision="fp32", fe=None, kT=1e-5,
                      omega=(1.2, 1.0, 1.0), seed=2,
                      name="D3Q19 ideal gas, 128^3 periodic, FP32 deviations, kT=1e-5, "
                           "omega=(1.2, 1.0, 1.0), shear wave + thermal start"),
 }
 # Algorithmic bytes per site of the fused step kernel: 19 pulled + 19 stored
-# populations (+ the density of the site for the non-ideal fluid); of the
-# density gather: 19 pulled populations + 1 density written.
+# populations.  The D3Q19 non-ideal kernel gathers the density it needs itself
+# (the re-reads of neighbouring populations come from L2), so its minimum DRAM
+# traffic is the same; the D2Q9 non-ideal step reads a density field written by
+# a separate gather kernel (Q pulled populations + 1 density written).
 ELEM = {"fp32": 4, "fp64": 8, "bf16": 2}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -55,15 +65,21 @@ def step_bytes(wl):
     e = ELEM[wl["precision"]]
     Q = wl["lattice"]
     rb = 8 if wl["precision"] == "fp64" else 4
-    fused = 2 * Q * e + (rb if wl["fe"] else 0)
-    gather = Q * e + rb
+    separate_gather = bool(wl["fe"]) and Q == 9
+    fused = 2 * Q * e + (rb if separate_gather else 0)
+    gather = Q * e + rb if separate_gather else 0
     return fused, gather
 
 
+KERNEL_SOURCES = ("flb_device.cuh", "flb_kernels.cuh", "flb_prec.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the sources the step kernels are compiled from (ncu counters taken
+    on other sources are stale)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1012_3632_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -318,7 +334,8 @@ def main():
         "data": "synthetic", "config": config_of(args, wl),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "k_step (fused pull + MRT collide + force + noise + store)",
+                     "kernel": "k_step_march" if (wl["fe"] and wl["lattice"] == 19) else "k_step",
+                     "what": "fused pull + moment-space MRT collide + Guo force + Philox/Box-Muller noise + store",
                      "bytes_per_site": fused_b, "sites_per_launch": V,
                      "avg_launch_ms": t_fused * 1e3},
         "kernels": {"density_gather": {"launches": int(kn[0]), "avg_ms": kms[0] / max(kn[0], 1),
@@ -326,7 +343,7 @@ def main():
                                        "achieved_gbs": gather_b * V / (kms[0] / max(kn[0], 1) * 1e-3) / 1e9
                                        if kn[0] else None},
                     "fused_step": {"launches": n_fused, "avg_ms": kms[1] / max(n_fused, 1)}},
-        "whole_step_gbs": (fused_b + (gather_b if wl["fe"] else 0)) * V / (ms_max / args.steps * 1e-3) / 1e9,
+        "whole_step_gbs": (fused_b + gather_b) * V / (ms_max / args.steps * 1e-3) / 1e9,
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launch,
     }
     if not args.no_cpu_baseline:

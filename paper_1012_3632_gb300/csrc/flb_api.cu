@@ -349,7 +349,7 @@ int flb_step(flb_ctx* c, int nsteps)
         void* dst = c->buf[c->cur ^ 1];
         size_t slot = 0;
         int rc;
-        if (c->m.nonideal) {
+        if (c->ops->step_needs_density(c->m)) {
             if ((rc = timer_begin(c, 0, &slot))) return rc;
             FLB_CUDA(c->ops->density(c->m, src, c->drho, c->stream));
             if ((rc = timer_end(c, slot))) return rc;

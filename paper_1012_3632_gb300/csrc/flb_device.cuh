@@ -40,30 +40,53 @@ __device__ __forceinline__ void store_s<float, __nv_bfloat16>(__nv_bfloat16* p, 
 // Counter-based random numbers
 // ---------------------------------------------------------------------------
 
+// Philox key schedule: the round keys k0 + r W0, k1 + r W1 (r = 0..9), computed
+// once on the host so that each round reads them from the parameter bank.
+struct PhiloxKeys {
+    uint32_t k[20];  // k[r] = k0 + r W0, k[10 + r] = k1 + r W1
+};
+
+inline PhiloxKeys philox_keys(uint64_t seed)
+{
+    PhiloxKeys K;
+    uint32_t k0 = (uint32_t)(seed & 0xffffffffu), k1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        K.k[r] = k0;
+        K.k[10 + r] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return K;
+}
+
 // Philox4x32 with 10 rounds (Salmon, Moraes, Dror & Shaw, SC'11).
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1)
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
+        // one 32x32 -> 64-bit multiply per word pair gives both halves
+        const unsigned long long p0 = 0xD2511F53ull * c.x;
+        const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ K.k[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ K.k[10 + r],
+                       (uint32_t)p0);
     }
     return c;
 }
 
 // Box-Muller on a pair of 32-bit words; uniforms (x + 1/2) 2^-32 lie in (0, 1].
+// Single precision uses the SFU intrinsics: log via __logf, the radius via
+// rsqrt, and cos/sin(2 pi u) = -cos/-sin(2 pi u - pi) with the argument in
+// [-pi, pi] where __sincosf is accurate to 2^-21.4 absolute.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1)
 {
     const float u0 = fmaf(__uint2float_rn(a), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float u1 = fmaf(__uint2float_rn(b), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float r = sqrtf(-2.0f * logf(u0));
+    const float t = fmaxf(-2.0f * __logf(u0), 1e-30f);  // u0 may round to 1: radius 0, not NaN
+    const float r = t * rsqrtf(t);
     float s, c;
-    sincospif(2.0f * u1, &s, &c);
-    z0 = r * c;
-    z1 = r * s;
+    __sincosf(fmaf(u1, 6.28318530717958648f, -3.14159265358979324f), &s, &c);
+    z0 = -r * c;
+    z1 = -r * s;
 }
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, double& z1)
 {
@@ -78,10 +101,10 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, d
 
 // Four standard normals from the call (site, step, call | tag << 8, replica).
 template <class R>
-__device__ __forceinline__ void normals4(uint32_t k0, uint32_t k1, uint32_t site, uint32_t step,
-                                         uint32_t call_tag, uint32_t replica, R z[4])
+__device__ __forceinline__ void normals4(const PhiloxKeys& K, uint32_t site, uint32_t step, uint32_t call_tag,
+                                         uint32_t replica, R z[4])
 {
-    const uint4 r = philox4x32_10(make_uint4(site, step, call_tag, replica), k0, k1);
+    const uint4 r = philox4x32_10(make_uint4(site, step, call_tag, replica), K);
     box_muller(r.x, r.y, z[0], z[1]);
     box_muller(r.z, r.w, z[2], z[3]);
 }
@@ -98,7 +121,7 @@ struct Coll {
     R sqrt_rho0;
     int noise;            // kT > 0
     int noise_local;      // local rho (1) or rho0 (0) in the noise variance
-    uint32_t k0, k1;      // Philox key
+    PhiloxKeys key;       // Philox round keys
     uint32_t step, replica;
 };
 
@@ -210,8 +233,8 @@ struct D2Q9 {
         if (P.noise) {
             const R sr = P.noise_local ? sqrt(rho) : P.sqrt_rho0;
             R z[8];
-            normals4(P.k0, P.k1, site, P.step, 0u, P.replica, z);
-            normals4(P.k0, P.k1, site, P.step, 1u, P.replica, z + 4);
+            normals4(P.key, site, P.step, 0u, P.replica, z);
+            normals4(P.key, site, P.step, 1u, P.replica, z + 4);
 #pragma unroll
             for (int k = 0; k < 6; ++k) Dm[3 + k] += P.ns[k] * sr * z[k];
         }
@@ -392,10 +415,10 @@ struct D3Q19 {
         if (P.noise) {
             const R sr = P.noise_local ? sqrt(rho) : P.sqrt_rho0;
             R z[16];
-            normals4(P.k0, P.k1, site, P.step, 0u, P.replica, z);
-            normals4(P.k0, P.k1, site, P.step, 1u, P.replica, z + 4);
-            normals4(P.k0, P.k1, site, P.step, 2u, P.replica, z + 8);
-            normals4(P.k0, P.k1, site, P.step, 3u, P.replica, z + 12);
+            normals4(P.key, site, P.step, 0u, P.replica, z);
+            normals4(P.key, site, P.step, 1u, P.replica, z + 4);
+            normals4(P.key, site, P.step, 2u, P.replica, z + 8);
+            normals4(P.key, site, P.step, 3u, P.replica, z + 12);
 #pragma unroll
             for (int k = 0; k < 15; ++k) Dm[4 + k] += P.ns[k] * sr * z[k];
         }

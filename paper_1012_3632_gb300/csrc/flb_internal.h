@@ -45,6 +45,7 @@ struct PrecOps {
                                  cudaStream_t);
     cudaError_t (*mode_field)(const HostModel&, const void* src, int mode, double2* out, cudaStream_t);
     int (*partial_rows_max)(const HostModel&);
+    int (*step_needs_density)(const HostModel&);
 };
 
 const PrecOps& ops_fp64();

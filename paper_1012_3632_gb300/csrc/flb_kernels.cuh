@@ -85,6 +85,34 @@ __device__ __forceinline__ void pull(const S* __restrict__ src, long V, const Nb
         g[i] = load_s<R>(src + (long)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i)));
 }
 
+// Base pointers of the Q population planes of the source and destination
+// buffers (in the parameter bank): a population address is one 32-bit site
+// offset from a per-direction base.
+template <class S>
+struct Planes {
+    const S* src[19];
+    S* dst[19];
+};
+
+template <class S>
+Planes<S> make_planes(const void* src, void* dst, int Q, long V)
+{
+    Planes<S> p{};
+    for (int i = 0; i < Q; ++i) {
+        p.src[i] = (const S*)src + (long)i * V;
+        p.dst[i] = (S*)dst + (long)i * V;
+    }
+    return p;
+}
+
+// Pull g_i(r - c_i) through the plane pointers.
+template <class L, class R, class S>
+__device__ __forceinline__ void pull_planes(const Planes<S>& P, const Nbhd& nb, R g[L::Q])
+{
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) g[i] = load_s<R>(P.src[i] + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i)));
+}
+
 // ---------------------------------------------------------------------------
 // Step parameters
 // ---------------------------------------------------------------------------
@@ -123,7 +151,7 @@ __global__ void k_density(const S* __restrict__ src, R* __restrict__ drho, int X
 // ---------------------------------------------------------------------------
 template <class L, class R, class S, bool NONIDEAL, int TX, int TY, int TZ>
 __global__ void __launch_bounds__(TX* TY* TZ)
-    k_step(const StepArgs<R> a, const S* __restrict__ src, S* __restrict__ dst, const R* __restrict__ drho)
+    k_step(const StepArgs<R> a, const __grid_constant__ Planes<S> P, const R* __restrict__ drho)
 {
     constexpr int HZ = (L::D == 3) ? 2 : 0;      // halo of rho in z
     constexpr int RX = TX + 4, RY = TY + 4, RZ = TZ + 2 * HZ;
@@ -181,17 +209,132 @@ __global__ void __launch_bounds__(TX* TY* TZ)
         F[2] = pre * gz;
     }
     if (x >= X || y >= Y || z >= Z) return;
-    const long V = a.V;
     const Nbhd nb(x, y, z, X, Y, Z);
     R g[L::Q];
-    pull<L>(src, V, nb, g);
+    pull_planes<L>(P, nb, g);
     const int s = x + X * (y + Y * z);
     if constexpr (L::D == 3)
         L::collide(g, F[0], F[1], F[2], a.c, (uint32_t)s);
     else
         L::collide(g, F[0], F[1], a.c, (uint32_t)s);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) store_s(dst + (long)i * V + s, g[i]);
+    for (int i = 0; i < L::Q; ++i) store_s(P.dst[i] + s, g[i]);
+}
+
+// ---------------------------------------------------------------------------
+// D3Q19 non-ideal fluid with the density gather fused in: one block owns a
+// TX x TY column of sites and marches over NZ planes in z.  Iteration k pulls
+// drho of plane zb+k+2 on the tile + 2-site halo (the tile interior's pulled
+// populations are re-read from L2 by the collision two planes later),
+// evaluates mu of plane zb+k+1 on the tile + 1-site halo, and collides plane
+// zb+k with F = -rho grad mu.  The first iterations (k < 0) only fill the
+// rings of 5 density planes and 3 chemical-potential planes kept in shared
+// memory; the density never goes to DRAM.  Each stage appears once in the
+// loop body so that the kernel stays small in the instruction cache.
+// ---------------------------------------------------------------------------
+template <class R, class S, int TX, int TY, int NZ, int MINB>
+__global__ void __launch_bounds__(TX* TY, MINB)
+    k_step_march(const StepArgs<R> a, const __grid_constant__ Planes<S> P)
+{
+    using L = D3Q19;
+    constexpr int NT = TX * TY, RX = TX + 4, RY = TY + 4, RP = RX * RY, MX = TX + 2, MY = TY + 2, MP = MX * MY;
+    constexpr int NRH = (RP + NT - 1) / NT;  // halo density sites per thread
+    __shared__ R srho[5][RP];
+    __shared__ R smu[3][MP];
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int X = a.X, Y = a.Y, Z = a.Z;
+    const int XY = X * Y;
+    const int xb = blockIdx.x * TX, yb = blockIdx.y * TY, zb = blockIdx.z * NZ;
+    const int nz = min(NZ, Z - zb);
+
+    // In-plane neighbourhood of this thread's density sites (fixed over z):
+    // x - 1, x, x + 1 and the row offsets X*(y - 1), X*y, X*(y + 1).
+    int hx[NRH][3], hy[NRH][3];
+#pragma unroll
+    for (int h = 0; h < NRH; ++h) {
+        const int e = min(tid + h * NT, RP - 1);
+        const int gx = wrap_any(xb - 2 + e % RX, X), gy = wrap_any(yb - 2 + e / RX, Y);
+        hx[h][0] = wrap_once(gx - 1, X);
+        hx[h][1] = gx;
+        hx[h][2] = wrap_once(gx + 1, X);
+        hy[h][0] = X * wrap_once(gy - 1, Y);
+        hy[h][1] = X * gy;
+        hy[h][2] = X * wrap_once(gy + 1, Y);
+    }
+
+    const int x = xb + threadIdx.x, y = yb + threadIdx.y;
+    const int cm = (threadIdx.x + 1) + MX * (threadIdx.y + 1);
+    const int cr = (threadIdx.x + 2) + RX * (threadIdx.y + 2);
+#pragma unroll 1
+    for (int k = -4; k < nz; ++k) {
+        // (1) density of plane zb+k+2 on the tile + 2 halo: drho = sum_i g*_i(r - c_i)
+        {
+            const int zc = wrap_any(zb + k + 2, Z);
+            const int zo[3] = {XY * wrap_once(zc - 1, Z), XY * zc, XY * wrap_once(zc + 1, Z)};
+            R* out = srho[(k + 4) % 5];
+#pragma unroll
+            for (int h = 0; h < NRH; ++h) {
+                const int e = tid + h * NT;
+                if (e < RP) {
+                    R g[L::Q], m[L::Q];
+#pragma unroll
+                    for (int i = 0; i < L::Q; ++i)
+                        g[i] = load_s<R>(P.src[i] + (hx[h][1 - Vel<L>::cx(i)] + hy[h][1 - Vel<L>::cy(i)] +
+                                                     zo[1 - Vel<L>::cz(i)]));
+                    L::moments(g, m);
+                    out[e] = m[0];
+                }
+            }
+        }
+        __syncthreads();
+        // (2) mu = psi'(rho) - kappa lap rho of plane zb+k+1 on the tile + 1 halo
+        if (k >= -2) {
+            const R* rm = srho[(k + 2) % 5];
+            const R* r0 = srho[(k + 3) % 5];
+            const R* rp = srho[(k + 4) % 5];
+            R* out = smu[(k + 2) % 3];
+            for (int e = tid; e < MP; e += NT) {
+                const int c = (e % MX + 1) + RX * (e / MX + 1);
+                const R rc = r0[c];
+                R lap = R(0);
+#pragma unroll
+                for (int i = 1; i < L::Q; ++i) {
+                    const int cz = Vel<L>::cz(i);
+                    const R* pl = cz > 0 ? rp : (cz < 0 ? rm : r0);
+                    lap += R(Vel<L>::w(i)) * (pl[c + Vel<L>::cx(i) + RX * Vel<L>::cy(i)] - rc);
+                }
+                lap *= R(6);
+                const R d = rc + a.rho0_minus_rhoc;
+                out[e] = d * (a.A + a.B * d * d) - a.kappa * lap;
+            }
+        }
+        __syncthreads();
+        // (3) collide plane zb+k with F = -rho grad mu, grad = 3 sum_i w_i c_i mu(r + c_i)
+        if (k >= 0 && x < X && y < Y) {
+            const int z = zb + k;
+            const R* mlo = smu[k % 3];
+            const R* mmid = smu[(k + 1) % 3];
+            const R* mhi = smu[(k + 2) % 3];
+            R gx = R(0), gy = R(0), gz = R(0);
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const int cz = Vel<L>::cz(i);
+                const R* pl = cz > 0 ? mhi : (cz < 0 ? mlo : mmid);
+                const R wm = R(Vel<L>::w(i)) * pl[cm + Vel<L>::cx(i) + MX * Vel<L>::cy(i)];
+                if (Vel<L>::cx(i)) gx += R(Vel<L>::cx(i)) * wm;
+                if (Vel<L>::cy(i)) gy += R(Vel<L>::cy(i)) * wm;
+                if (Vel<L>::cz(i)) gz += R(Vel<L>::cz(i)) * wm;
+            }
+            const R pre = R(-3) * (a.c.rho0 + srho[(k + 2) % 5][cr]);
+            const Nbhd nb(x, y, z, X, Y, Z);
+            R g[L::Q];
+            pull_planes<L>(P, nb, g);
+            const int s = x + X * (y + Y * z);
+            L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s);
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) store_s(P.dst[i] + s, g[i]);
+        }
+    }
 }
 
 }  // namespace flb

@@ -9,6 +9,13 @@
 #include "flb_internal.h"
 #include "flb_kernels.cuh"
 
+#ifndef FLB_MARCH_MINB
+#define FLB_MARCH_MINB 3
+#endif
+#ifndef FLB_MARCH_NZ
+#define FLB_MARCH_NZ 32
+#endif
+
 namespace flb {
 
 // ---------------------------------------------------------------------------
@@ -35,8 +42,7 @@ Coll<R> make_coll(const HostModel& m, uint64_t step)
     c.sqrt_rho0 = R(std::sqrt(m.rho0));
     c.noise = m.kT > 0.0;
     c.noise_local = m.noise_local;
-    c.k0 = (uint32_t)(m.seed & 0xffffffffu);
-    c.k1 = (uint32_t)(m.seed >> 32);
+    c.key = philox_keys(m.seed);
     c.step = (uint32_t)step;
     c.replica = m.replica;
     return c;
@@ -105,7 +111,7 @@ __global__ void k_init(const StepArgs<R> a, S* __restrict__ dst, const double* _
         R zz[4 * L::NCALL_ALL];
 #pragma unroll
         for (int b = 0; b < L::NCALL_ALL; ++b)
-            normals4(a.c.k0, a.c.k1, (uint32_t)s, 0u, (uint32_t)b | (1u << 8), a.c.replica, zz + 4 * b);
+            normals4(a.c.key, (uint32_t)s, 0u, (uint32_t)b | (1u << 8), a.c.replica, zz + 4 * b);
 #pragma unroll
         for (int q = 0; q < L::Q; ++q) m[q] += amp.tn[q] * sr * zz[q];
     }
@@ -336,17 +342,22 @@ struct Prec {
     {
         const StepArgs<R> a = make_args<L, R>(m, step);
         const dim3 b(TX, TY, TZ);
-        k_step<L, R, S, NI, TX, TY, TZ><<<grid_for(m, b), b, 0, st>>>(a, (const S*)src, (S*)dst, (const R*)drho);
+        k_step<L, R, S, NI, TX, TY, TZ><<<grid_for(m, b), b, 0, st>>>(a, make_planes<S>(src, dst, L::Q, m.V),
+                                                                       (const R*)drho);
         return cudaGetLastError();
     }
     static cudaError_t step(const HostModel& m, uint64_t t, const void* src, void* dst, const void* drho,
                             cudaStream_t st)
     {
         if (m.Q == 19) {
-            // double needs more registers per thread: smaller tiles avoid spills
             if (m.nonideal) {
-                if (sizeof(R) == 8) return step_t<D3Q19, true, 32, 4, 2>(m, t, src, dst, drho, st);
-                return step_t<D3Q19, true, 32, 4, 4>(m, t, src, dst, drho, st);
+                constexpr int TX = 32, TY = 8, NZ = FLB_MARCH_NZ;
+                const StepArgs<R> a = make_args<D3Q19, R>(m, t);
+                const dim3 b(TX, TY, 1);
+                const dim3 g((m.X + TX - 1) / TX, (m.Y + TY - 1) / TY, (m.Z + NZ - 1) / NZ);
+                k_step_march<R, S, TX, TY, NZ, (sizeof(R) == 8 ? 1 : FLB_MARCH_MINB)>
+                    <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
+                return cudaGetLastError();
             }
             return step_t<D3Q19, false, 32, 4, 2>(m, t, src, dst, drho, st);
         }
@@ -420,6 +431,9 @@ struct Prec {
     {
         return m.Q == 19 ? mu_force_l<D3Q19>(m, drho, mu, F, st) : mu_force_l<D2Q9>(m, drho, mu, F, st);
     }
+    // The D2Q9 non-ideal step reads a density field gathered beforehand; the
+    // D3Q19 one gathers the density itself.
+    static int needs_density(const HostModel& m) { return m.nonideal && m.Q == 9; }
     static int rows(const HostModel& m)
     {
         const dim3 b = m.Q == 19 ? site_block<D3Q19>() : site_block<D2Q9>();
@@ -467,7 +481,7 @@ struct Prec {
     static const PrecOps& ops()
     {
         static const PrecOps o = {(int)sizeof(S), (int)sizeof(R), density, step, init, get_pop, set_pop, moments,
-                                  mu_force, mode_partials, cons_partials, mode_field, rows};
+                                  mu_force, mode_partials, cons_partials, mode_field, rows, needs_density};
         return o;
     }
 };

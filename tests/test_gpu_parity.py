@@ -211,13 +211,15 @@ def test_checkpoint_resume_is_bitwise(tmp_path, prec):
     assert np.array_equal(fa, fb)
 
 
-def test_kernel_timing_counts_launches():
-    with Context(19, (32, 16, 8), precision="fp32", free_energy=FE, kT=1e-6, omega_shear=1.0) as ctx:
-        ctx.init(rho=inputs.uniform_density((32, 16, 8)))
+@pytest.mark.parametrize("Q,dims,gathers", [(19, (32, 16, 8), 0), (9, (32, 16, 1), 5)])
+def test_kernel_timing_counts_launches(Q, dims, gathers):
+    """D3Q19 gathers the density inside the fused kernel; D2Q9 runs a gather kernel first."""
+    with Context(Q, dims, precision="fp32", free_energy=FE, kT=1e-6, omega_shear=1.0) as ctx:
+        ctx.init(rho=inputs.uniform_density(dims))
         ctx.kernel_timing(True)
         ctx.step(5)
         ms, n = ctx.kernel_times()
-        assert list(n[:2]) == [5, 5] and ms[0] > 0 and ms[1] > 0
+        assert list(n[:2]) == [gathers, 5] and ms[1] > 0 and (ms[0] > 0) == (gathers > 0)
 
 
 def test_divergence_is_reported():
