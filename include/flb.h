@@ -195,6 +195,33 @@ int flb_get_info(flb_ctx* ctx, int out[6]);
 int flb_kernel_timing(flb_ctx* ctx, int enable);
 int flb_kernel_times(flb_ctx* ctx, double* ms, int* launches);
 
+/* Structure factor that allocates nothing.  For callers that cannot allocate
+ * device memory while they run -- code captured into a CUDA graph, hosts whose
+ * allocator forbids cudaMalloc after start-up, real-time loops with a fixed
+ * memory budget -- this computes, from buffers the caller already owns, the
+ * same S_a(k) as flb_structure_factor (accumulate = 0).  The paper has no
+ * counterpart: it is an interface variant of flb_structure_factor.
+ *   lattice  FLB_D2Q9 or FLB_D3Q19;  dims as in flb_create, with at most
+ *            FLB_NOALLOC_MAX_SITES sites and every edge a product of 2, 3 and 5
+ *            (up to 4096); anything else returns FLB_EINVAL before any GPU work
+ *   f        device pointer: pre-collision populations f^LB, Q*V doubles in the
+ *            layout f[i*V + s] (what flb_get_populations returns), read only
+ *   mode     0 = density, else the mode index of the basis above
+ *   S        device pointer to V doubles, overwritten with S_a(k) (S_a(0) = 0)
+ *   stream   cudaStream_t to enqueue on (NULL: legacy default stream); the
+ *            call returns after enqueueing, without synchronising
+ * The FFT work array is a static device array of FLB_NOALLOC_MAX_SITES complex
+ * doubles (16 MiB) that every GPU which loads the library holds until the
+ * process exits.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current: make that first
+ * call before any stream capture.  Every call uses the same array, so calls
+ * that may overlap on the GPU (unordered streams) race and must be serialised
+ * by the caller.  No cudaMalloc, cudaFree or allocating library routine is
+ * called. */
+#define FLB_NOALLOC_MAX_SITES (1 << 20)
+int flb_structure_factor_noalloc(int lattice, const int dims[3], const double* f, int mode, double* S,
+                                 void* stream);
+
 /* Checkpoint: parameters, step counter, seed, replica and the populations in
  * the stored precision; a resumed run continues bit for bit. */
 int flb_save(flb_ctx* ctx, const char* path);

@@ -23,6 +23,14 @@ int fail(int code, const std::string& msg)
     return code;
 }
 
+}  // namespace
+
+namespace flb {
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+}  // namespace flb
+
+namespace {
+
 #define FLB_CUDA(call)                                                                              \
     do {                                                                                            \
         cudaError_t e_ = (call);                                                                    \

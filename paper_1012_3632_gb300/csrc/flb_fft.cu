@@ -209,6 +209,12 @@ __global__ void k_dft_lines_naive(const double2* __restrict__ in, double2* __res
     }
 }
 
+bool fft_length_in_place(int L)
+{
+    FftPlan p;
+    return L == 1 || (L <= 4096 && make_plan(L, p));
+}
+
 static cudaError_t fft_axis(double2* data, double2* scratch, int L, long es, long s_in, int n_in, long s_out,
                             int n_out, long V, cudaStream_t s)
 {

@@ -4,6 +4,8 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+
 #include <cuda_runtime.h>
 
 namespace flb {
@@ -54,6 +56,13 @@ const PrecOps& ops_bf16();
 
 // Deterministic column sums: out[c] = sum_r partials[r*ncol + c] (flb_fft.cu).
 cudaError_t sum_columns(const double* partials, int nrows, int ncol, double* out, cudaStream_t s);
+
+// True when an axis of length L is transformed by the in-place mixed-radix FFT
+// (L a product of 2, 3 and 5, at most 4096); other lengths need `scratch`.
+bool fft_length_in_place(int L);
+
+// Record the calling thread's last error message (flb_last_error) and return code.
+int set_error(int code, const std::string& msg);
 
 // In-place forward DFT along every axis of length > 1 of a complex X*Y*Z field.
 cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s);

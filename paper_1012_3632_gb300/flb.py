@@ -31,8 +31,9 @@ EXPORTS = [
     "flb_snapshot_count", "flb_reset_accumulators", "flb_conservation", "flb_get_populations",
     "flb_set_populations", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
     "flb_get_info", "flb_kernel_timing", "flb_kernel_times", "flb_save", "flb_load", "flb_error_string",
-    "flb_last_error", "flb_destroy",
+    "flb_last_error", "flb_destroy", "flb_structure_factor_noalloc",
 ]
+NOALLOC_MAX_SITES = 1 << 20
 
 
 class FLBError(RuntimeError):
@@ -89,6 +90,7 @@ def lib():
         "flb_error_string": (ctypes.c_char_p, [ctypes.c_int]),
         "flb_last_error": (ctypes.c_char_p, []),
         "flb_destroy": (None, [vp]),
+        "flb_structure_factor_noalloc": (ctypes.c_int, [ctypes.c_int, ip, vp, ctypes.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
