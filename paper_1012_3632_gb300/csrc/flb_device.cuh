@@ -36,6 +36,25 @@ __device__ __forceinline__ void store_s<float, __nv_bfloat16>(__nv_bfloat16* p, 
     *p = __float2bfloat16_rn(v);
 }
 
+// Streaming variants for the time step: a stored population is not read again
+// before the next step, and the last read of a population within a step need
+// not stay in L2 (evict-first / last-use hints keep L2 for data still to be
+// re-read).
+template <class R, class S>
+__device__ __forceinline__ void store_stream(S* p, R v) { __stcs(p, static_cast<S>(v)); }
+template <>
+__device__ __forceinline__ void store_stream<float, __nv_bfloat16>(__nv_bfloat16* p, float v)
+{
+    __stcs(reinterpret_cast<unsigned short*>(p), __bfloat16_as_ushort(__float2bfloat16_rn(v)));
+}
+template <class R, class S>
+__device__ __forceinline__ R load_last(const S* p) { return static_cast<R>(__ldlu(p)); }
+template <>
+__device__ __forceinline__ float load_last<float, __nv_bfloat16>(const __nv_bfloat16* p)
+{
+    return __bfloat162float(__ushort_as_bfloat16(__ldlu(reinterpret_cast<const unsigned short*>(p))));
+}
+
 // ---------------------------------------------------------------------------
 // Counter-based random numbers
 // ---------------------------------------------------------------------------

@@ -105,12 +105,16 @@ Planes<S> make_planes(const void* src, void* dst, int Q, long V)
     return p;
 }
 
-// Pull g_i(r - c_i) through the plane pointers.
-template <class L, class R, class S>
+// Pull g_i(r - c_i) through the plane pointers (LAST: last read of these
+// populations in this step).
+template <class L, bool LAST, class R, class S>
 __device__ __forceinline__ void pull_planes(const Planes<S>& P, const Nbhd& nb, R g[L::Q])
 {
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) g[i] = load_s<R>(P.src[i] + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i)));
+    for (int i = 0; i < L::Q; ++i) {
+        const S* p = P.src[i] + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i));
+        g[i] = LAST ? load_last<R>(p) : load_s<R>(p);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -211,14 +215,14 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     if (x >= X || y >= Y || z >= Z) return;
     const Nbhd nb(x, y, z, X, Y, Z);
     R g[L::Q];
-    pull_planes<L>(P, nb, g);
+    pull_planes<L, false>(P, nb, g);
     const int s = x + X * (y + Y * z);
     if constexpr (L::D == 3)
         L::collide(g, F[0], F[1], F[2], a.c, (uint32_t)s);
     else
         L::collide(g, F[0], F[1], a.c, (uint32_t)s);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) store_s(P.dst[i] + s, g[i]);
+    for (int i = 0; i < L::Q; ++i) store_stream(P.dst[i] + s, g[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -328,11 +332,11 @@ __global__ void __launch_bounds__(TX* TY, MINB)
             const R pre = R(-3) * (a.c.rho0 + srho[(k + 2) % 5][cr]);
             const Nbhd nb(x, y, z, X, Y, Z);
             R g[L::Q];
-            pull_planes<L>(P, nb, g);
+            pull_planes<L, true>(P, nb, g);
             const int s = x + X * (y + Y * z);
             L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s);
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i) store_s(P.dst[i] + s, g[i]);
+            for (int i = 0; i < L::Q; ++i) store_stream(P.dst[i] + s, g[i]);
         }
     }
 }

@@ -1,0 +1,128 @@
+"""Statistical and hydrodynamic checks of the GPU path against what the paper fixes.
+
+- Equal-time variance of every mode, ghosts included, equals its ideal-gas FDT
+  value rho0 kT N_a / cs^2 (Eqs. (G-ideal), (mu-ideal), (noise-lbe)): mode
+  temperatures T_a = cs^2 <dm_a^2> / (rho0 N_a) = kT within 1% over 10^4 steps
+  on the 128^3 shear-wave workload.
+- Shear-wave amplitude decays as exp(-nu k^2 t), nu = cs^2 (1/omega - 1/2)
+  (App. B with the lambda^LB map of Sec. V).
+- Ideal gas: S(k) = rho0 kT / cs^2 at every k (Eq. (S-ideal)).
+- Force-based non-ideal fluid: momentum and every non-conserved mode keep their
+  ideal variances (Eq. (g-mat-forcing)); S(k) follows the Ornstein-Zernike form
+  rho0 kT / c_s^2(k), c_s^2(k) = cs^2 + rho0 psi''(rho0) + kappa rho0 k^2
+  (Eq. (he-cs2)) at small k.
+"""
+import numpy as np
+import pytest
+
+from paper_1012_3632_gb300 import MODE_VAR, U, Context, inputs
+
+pytestmark = pytest.mark.gpu
+
+CS2 = 1.0 / 3.0
+N19 = np.array([1, 1 / 3, 1 / 3, 1 / 3, 2 / 3, 4 / 3, 4 / 9, 1 / 9, 1 / 9, 1 / 9, 2 / 27, 2 / 27, 2 / 27,
+                2 / 9, 2 / 9, 2 / 9, 2 / 9, 1 / 3, 1 / 9])
+
+
+def _kgrid(dims):
+    ks = [2 * np.pi * np.fft.fftfreq(n) for n in dims]  # components in [-pi, pi)
+    kz, ky, kx = np.meshgrid(ks[2], ks[1], ks[0], indexing="ij")
+    return kx.reshape(-1), ky.reshape(-1), kz.reshape(-1)
+
+
+@pytest.fixture(scope="module")
+def config1_run():
+    """128^3 D3Q19 ideal gas, FP32, kT = 1e-5, rates (1.2, 1.0, 1.0), shear wave
+    u_x = 1e-3 sin(2 pi z / 128) plus thermal start, 10^4 steps; snapshots
+    every 100 steps."""
+    dims = (128, 128, 128)
+    kT, om = 1e-5, 1.2
+    u = inputs.shear_wave(dims, amp=1e-3)
+    z = np.repeat(np.arange(dims[2]), dims[0] * dims[1])
+    sinz = np.sin(2 * np.pi * z / dims[2])
+    amps, times = [], []
+    with Context(19, dims, om, 1.0, 1.0, kT=kT, seed=2, precision="fp32") as ctx:
+        ctx.init(u=u, thermal=True)
+        var = None
+        for t in range(100, 10001, 100):
+            ctx.step(100)
+            var = ctx.moments(MODE_VAR)
+            ctx.structure_factor(1, accumulate=True, fetch=False)
+            ux = ctx.moments(U)[0]
+            amps.append(2.0 * (ux @ sinz) / ux.size)
+            times.append(t)
+        Sjx = ctx.structure_factor(1, accumulate=True)  # one more snapshot, returns the mean
+    return dict(dims=dims, kT=kT, om=om, var=var, Sjx=Sjx, amps=np.array(amps), times=np.array(times))
+
+
+def test_mode_temperatures_within_one_percent(config1_run):
+    r = config1_run
+    V = np.prod(r["dims"])
+    T = CS2 * r["var"] / N19 / r["kT"]
+    # j_x carries the deterministic wave: take its variance from the spectrum
+    # without k = 0 and the wave's two wavevectors (0, 0, +-1)
+    kx, ky, kz = _kgrid(r["dims"])
+    wave = (kx == 0) & (ky == 0) & (np.abs(np.abs(kz) - 2 * np.pi / r["dims"][2]) < 1e-12)
+    keep = ~wave
+    keep[0] = False
+    var_jx = r["Sjx"][keep].sum() / V * V / keep.sum()
+    T[1] = CS2 * var_jx / N19[1] / r["kT"]
+    assert np.all(np.abs(T - 1.0) < 0.01), T
+
+
+def test_shear_wave_decay_rate(config1_run):
+    r = config1_run
+    k = 2 * np.pi / r["dims"][2]
+    nu = CS2 * (1.0 / r["om"] - 0.5)
+    # the thermal fluctuation of the same Fourier mode (~3e-6, correlated over
+    # ~1/(nu k^2) = 3700 steps) rides on the amplitude: fit while the wave is
+    # at least 40% of its initial size
+    a = r["amps"]
+    sel = a > 0.4 * a[0]
+    rate = -np.polyfit(r["times"][sel], np.log(a[sel]), 1)[0]
+    assert abs(rate / (nu * k * k) - 1) < 0.01, (rate, nu * k * k)
+
+
+def test_ideal_gas_structure_factor_flat():
+    """S(k) = rho0 kT / cs^2 for every k of a thermalised ideal gas (64^3, 3000 steps)."""
+    dims = (64, 64, 64)
+    kT = 1e-5
+    with Context(19, dims, 1.3, 0.8, 1.5, kT=kT, seed=11, precision="fp32") as ctx:
+        ctx.init(thermal=True)
+        for _ in range(60):
+            ctx.step(50)
+            S = ctx.structure_factor(0, accumulate=True)
+    ratio = S[1:] / (kT / CS2)
+    assert abs(ratio.mean() - 1) < 0.01, ratio.mean()
+    kx, ky, kz = _kgrid(dims)
+    kk = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)[1:]
+    for lo, hi in ((0.0, 1.0), (1.0, 2.0), (2.0, 3.0), (3.0, 6.0)):
+        m = (kk >= lo) & (kk < hi)
+        assert abs(ratio[m].mean() - 1) < 0.03, (lo, hi, ratio[m].mean())
+
+
+def test_nonideal_fluid_equilibrium():
+    """Force-based fluid (A=-0.01, B=0.1, rho_c=1, kappa=0.02) at 64^3, FP32,
+    kT = 1e-5, thermal start: momentum and non-conserved modes at kT; density
+    structure factor Ornstein-Zernike at |k| < 0.5."""
+    dims = (64, 64, 64)
+    kT = 1e-5
+    A, kappa = -0.01, 0.02
+    fe = dict(A=A, B=0.1, rho_c=1.0, kappa=kappa)
+    with Context(19, dims, 1.0, 1.0, 1.0, kT=kT, seed=13, precision="fp32", free_energy=fe) as ctx:
+        ctx.init(thermal=True)
+        ctx.step(2000)
+        for _ in range(200):
+            ctx.step(100)
+            S = ctx.structure_factor(0, accumulate=True, fetch=False)
+            var = ctx.moments(MODE_VAR)
+        S = ctx.structure_factor(0, accumulate=True)
+    T = CS2 * var / N19 / kT
+    assert np.all(np.abs(T[1:4] - 1) < 0.01), T[1:4]          # momentum
+    assert np.all(np.abs(T[4:] - 1) < 0.02), T[4:]            # stress and ghost modes
+    kx, ky, kz = _kgrid(dims)
+    k2 = kx ** 2 + ky ** 2 + kz ** 2
+    small = (k2 > 0) & (k2 < 0.25)
+    oz = kT / (CS2 + A + kappa * k2[small])
+    ratio = S[small] / oz
+    assert abs(ratio.mean() - 1) < 0.02, ratio.mean()
