@@ -41,6 +41,9 @@ WORKLOADS = {
                         omega=(1.0, 1.0, 1.0), seed=3,
                         name="D3Q19 force-based non-ideal fluid, 128^3 periodic, FP32 deviations, "
                              "parameters of the 256^3 workload (profiling size)"),
+    "nonideal256x256x128": dict(lattice=19, dims=(256, 256, 128), precision="fp32", fe=FE, kT=1e-6,
+                                omega=(1.0, 1.0, 1.0), seed=3,
+                                name="D3Q19 force-based non-ideal fluid, 256x256x128, FP32 (profiling size)"),
     "ideal256": dict(lattice=19, dims=(256, 256, 256), precision="fp32", fe=None, kT=1e-5,
                      omega=(1.2, 1.0, 1.0), seed=2,
                      name="D3Q19 ideal gas, 256^3 periodic, FP32 deviations, kT=1e-5, "
@@ -177,6 +180,98 @@ def cpu_baseline(wl, budget_s=12.0):
                       f"FP64 C oracle, single thread"}
 
 
+def batched_vs_plain(n=64, steps=200, seed=4):
+    """Batched ensemble (64 D3Q19 ideal-gas replicas, cubic sizes drawn from
+    {32,48,64,96,128}, omega_shear ~ U(0.8,1.6), kT = 1e-5, FP32, one persistent
+    launch per step replayed from a CUDA graph) against the plain single-lattice
+    step on the same replicas.  Returns site updates per second of both."""
+    import numpy as np
+    import torch
+
+    from paper_1012_3632_gb300 import Batch, Context, inputs
+
+    L = inputs.replica_sizes(n, seed=seed)
+    om = inputs.replica_omegas(n, seed=seed)
+    dims = [(int(l), int(l), int(l)) for l in L]
+    sites = int(sum(l ** 3 for l in L))
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Batch(dims, om, [1e-5] * n, [1000 + r for r in range(n)], stream=stream.cuda_stream) as b:
+        b.init(thermal=True)
+        shapes = b.autotune()
+        b.step(20)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        b.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = ev0.elapsed_time(ev1) / steps  # ms per ensemble step
+    # plain: one context per replica size, time per step times the count
+    t_plain = 0.0
+    for l in sorted(set(int(v) for v in L)):
+        cnt = int((L == l).sum())
+        with Context(19, (l, l, l), 1.2, kT=1e-5, seed=1, precision="fp32", stream=stream.cuda_stream) as c:
+            c.init(thermal=True)
+            c.step(10)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            c.step(50)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t_plain += cnt * ev0.elapsed_time(ev1) / 50
+    shape_of = {int(l): [int(v) for v in shapes[int(np.where(L == l)[0][0])]] for l in set(int(v) for v in L)}
+    return {"workload": f"{n} D3Q19 ideal-gas replicas, cubic sizes from {{32,48,64,96,128}} (seed {seed}), "
+                        "omega_shear U(0.8,1.6), kT=1e-5, FP32, graph-replayed persistent launch",
+            "sites": sites, "batched_mlups": sites / (t_batch * 1e-3) / 1e6,
+            "plain_mlups": sites / (t_plain * 1e-3) / 1e6, "batched_over_plain": t_plain / t_batch,
+            "ms_per_ensemble_step": t_batch, "tile_shape_per_size": shape_of}
+
+
+def adjoint_vs_plain(dims=(64, 64, 64), nsteps=200, every=20, precision="fp32"):
+    """Gradient workload: the 64^3 non-ideal fluid (parameters of the 256^3
+    workload), 200 steps with checkpoints every 20, loss sum_k |rho_hat|^2
+    exp(-k^2/0.5) at the last step.  Times the forward pass (steps +
+    checkpoint copies), the backward pass (recomputation + adjoint steps) and
+    the plain step on the same lattice."""
+    import torch
+
+    from paper_1012_3632_gb300 import Context, inputs
+    from paper_1012_3632_gb300.adjoint import density_spectrum_loss, run
+
+    V = dims[0] * dims[1] * dims[2]
+    dt = torch.float32 if precision == "fp32" else torch.float64
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    with Context(19, dims, 1.0, 1.0, 1.0, kT=1e-6, free_energy=FE, seed=5, precision=precision,
+                 stream=stream.cuda_stream) as c:
+        c.init(rho=inputs.uniform_density(dims, seed=5))
+        c.step(20)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        c.step(nsteps)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t_plain = ev[0].elapsed_time(ev[1]) / nsteps
+        g0 = torch.empty((19, V), dtype=dt, device="cuda")
+        c.get_state_device(g0.data_ptr())
+    cfg = dict(dims=dims, kT=1e-6, seed=5, precision=precision, nsteps=nsteps, every=every, nonideal=True, rho_c=1.0)
+    theta = torch.tensor([1.0, 1.0, 1.0, 0.02, -0.01, 0.1], dtype=torch.float64, requires_grad=True)
+    g = g0.clone().requires_grad_(True)
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    loss = density_spectrum_loss(run(g, theta, cfg), dims)
+    ev[1].record(stream)
+    loss.backward()
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    t_fwd = ev[0].elapsed_time(ev[1]) / nsteps
+    t_bwd = ev[1].elapsed_time(ev[2]) / nsteps
+    return {"workload": f"D3Q19 non-ideal {dims[0]}x{dims[1]}x{dims[2]} {precision.upper()}, {nsteps} steps, "
+                        f"checkpoints every {every}, spectral density loss",
+            "plain_ms_per_step": t_plain, "forward_ms_per_step": t_fwd, "backward_ms_per_step": t_bwd,
+            "backward_over_plain": t_bwd / t_plain, "grad_theta": [float(v) for v in theta.grad]}
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return
@@ -227,6 +322,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="nonideal256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-replica comparison")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -346,6 +442,9 @@ def main():
         "whole_step_gbs": (fused_b + gather_b) * V / (ms_max / args.steps * 1e-3) / 1e9,
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launch,
     }
+    if not args.no_batched:
+        line["batched"] = batched_vs_plain()
+        line["adjoint"] = adjoint_vs_plain()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
     print(json.dumps(line))

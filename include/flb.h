@@ -173,6 +173,31 @@ int flb_conservation(flb_ctx* ctx, double out[4]);
 int flb_get_populations(flb_ctx* ctx, double* f);
 int flb_set_populations(flb_ctx* ctx, const double* f);
 
+/* ---- Adjoint -----------------------------------------------------------------
+ * Device-side state exchange and the adjoint (reverse-mode derivative) of one
+ * D3Q19 time step, for gradient-based use (e.g. behind an autograd function
+ * with checkpointing).  The paper derives no adjoint; the step differentiated
+ * is exactly the forward update of flb_step (Eq. (lbe-mom), the force model of
+ * App. A and the noise with its local-density amplitude, replayed from the
+ * same Philox counters).
+ *
+ * State buffers are caller-owned device arrays of 19*V elements of the storage
+ * type (double for FLB_FP64, float for FLB_FP32) holding pre-collision
+ * deviations g_i = f_i - w_i rho0 in the layout g[i*V + s]. */
+
+/* Copy the current state into g (enqueued, no synchronisation). */
+int flb_get_state_device(flb_ctx* ctx, void* g);
+/* Replace the current state by g (enqueued, no synchronisation). */
+int flb_set_state_device(flb_ctx* ctx, const void* g);
+
+/* Given the state g_n at time `step` and lam_next = dJ/dg at time step+1,
+ * write lam = dJ/dg at time `step` (must not alias lam_next) and add to the
+ * device array grad[6] the derivatives dJ/d(omega_shear, omega_bulk,
+ * omega_ghost, kappa, A, B) contributed by this step.  D3Q19, FP64 or FP32
+ * contexts only (FLB_EINVAL otherwise).  Work arrays are allocated on first
+ * use.  Enqueued on the context's stream. */
+int flb_adjoint_step(flb_ctx* ctx, const void* g_n, uint64_t step, const void* lam_next, void* lam, double* grad);
+
 /* Step counter (the time index keying the collision noise). */
 int flb_get_step(flb_ctx* ctx, uint64_t* step);
 int flb_set_step(flb_ctx* ctx, uint64_t step);
@@ -194,6 +219,54 @@ int flb_get_info(flb_ctx* ctx, int out[6]);
 #define FLB_NKERNEL_TIMERS 3
 int flb_kernel_timing(flb_ctx* ctx, int enable);
 int flb_kernel_times(flb_ctx* ctx, double* ms, int* launches);
+
+/* ---- Batched replicas -------------------------------------------------------
+ * Up to FLB_BATCH_MAX independent periodic D3Q19 ideal-gas lattices of uneven
+ * sizes, advanced together for ensemble averages (the equilibration-ratio
+ * statistics of Sec. VI).  Each time step is one persistent kernel launch over
+ * the flattened (replica, tile) work list; steps are replayed from a captured
+ * CUDA graph of two steps.  Populations are FP32 deviations.  Replica r uses
+ * the Philox key seeds[r] and counter word replica = opt->replica + r, so its
+ * noise is that of a single context created with the same seed and replica
+ * word.  Observables are per replica. */
+#define FLB_BATCH_MAX 96
+typedef struct flb_batch flb_batch;
+
+/* n replicas; dims: n*3 ints; omega_shear, kT, seeds: n values; omega_bulk and
+ * omega_ghost: n values or NULL (1.0).  opt: precision must be FLB_FP32 (the
+ * default); rho0, replica, noise_rho_local, stream and device as for
+ * flb_create.  State: rest at step 0.  FLB_EINVAL for bad arguments. */
+int flb_batch_create(flb_batch** out, int lattice, int n, const int* dims, const double* omega_shear,
+                     const double* omega_bulk, const double* omega_ghost, const double* kT,
+                     const uint64_t* seeds, const flb_options* opt);
+
+/* Rest state f = w rho0 in every replica, plus the thermal modes of flb_init
+ * when thermal_init != 0; resets the step counter and the accumulators. */
+int flb_batch_init(flb_batch* b, int thermal_init);
+
+/* Advance every replica nsteps time steps (graph replays of two steps). */
+int flb_batch_step(flb_batch* b, int nsteps);
+
+/* Time each candidate tile shape (x, y, z; 256 sites, powers of two) on the
+ * replicas of each distinct lattice size and keep the fastest per size; the
+ * state is not advanced.  shapes (n*3 ints, may be NULL) receives the choice. */
+int flb_batch_autotune(flb_batch* b, int* shapes);
+
+/* Add the current state to the per-replica snapshot accumulators and return in
+ * out[r*19 + a] the mean over snapshots of (1/V_r) sum (m_a - <m_a>)^2. */
+int flb_batch_mode_variance(flb_batch* b, double* out);
+
+/* Structure factor of one replica, as flb_structure_factor. */
+int flb_batch_structure_factor(flb_batch* b, int replica, double* S, int mode, int accumulate);
+
+/* Pre-collision populations of one replica (host, 19*V_r doubles). */
+int flb_batch_get_populations(flb_batch* b, int replica, double* f);
+
+/* Number of replicas, total sites, step counter (each may be NULL). */
+int flb_batch_info(flb_batch* b, int* n, long long* sites, uint64_t* step);
+
+int flb_batch_synchronize(flb_batch* b);
+void flb_batch_destroy(flb_batch* b);
 
 /* Structure factor that allocates nothing.  For callers that cannot allocate
  * device memory while they run -- code captured into a CUDA graph, hosts whose

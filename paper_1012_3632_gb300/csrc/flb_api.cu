@@ -84,6 +84,11 @@ struct flb_ctx {
     std::vector<double> mv_sum;         // per-mode sum over snapshots of the site variance
     int mv_count = 0;
 
+    // adjoint scratch
+    void* adj_work = nullptr;
+    double* adj_rows = nullptr;
+    double* adj_col = nullptr;
+
     // kernel timing
     bool timing = false;
     double t_ms[FLB_NKERNEL_TIMERS] = {0, 0, 0};
@@ -112,7 +117,8 @@ int alloc(void** p, size_t bytes)
 
 void free_all(flb_ctx* c)
 {
-    void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp};
+    void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
+                    c->adj_work, c->adj_rows, c->adj_col};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (double* p : c->sk_acc)
@@ -521,6 +527,39 @@ int flb_set_populations(flb_ctx* c, const double* f)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
     if (e != cudaSuccess) return fail(FLB_ECUDA, std::string("flb_set_populations: ") + cudaGetErrorString(e));
+    return FLB_OK;
+}
+
+int flb_get_state_device(flb_ctx* c, void* g)
+{
+    if (!c || !g) return fail(FLB_EINVAL, "ctx or g is NULL");
+    DeviceGuard guard(c->device);
+    FLB_CUDA(c->ops->pull_state(c->m, c->buf[c->cur], g, c->stream));
+    return FLB_OK;
+}
+
+int flb_set_state_device(flb_ctx* c, const void* g)
+{
+    if (!c || !g) return fail(FLB_EINVAL, "ctx or g is NULL");
+    DeviceGuard guard(c->device);
+    FLB_CUDA(c->ops->push_state(c->m, g, c->buf[c->cur], c->stream));
+    return FLB_OK;
+}
+
+int flb_adjoint_step(flb_ctx* c, const void* g_n, uint64_t step, const void* lam_next, void* lam, double* grad)
+{
+    if (!c || !g_n || !lam_next || !lam || !grad) return fail(FLB_EINVAL, "NULL argument");
+    if (c->m.Q != 19) return fail(FLB_EINVAL, "the adjoint step is implemented for D3Q19");
+    if (c->prec == FLB_BF16) return fail(FLB_EINVAL, "the adjoint step needs FLB_FP64 or FLB_FP32 storage");
+    if (lam == lam_next) return fail(FLB_EINVAL, "lam and lam_next must not alias");
+    DeviceGuard guard(c->device);
+    int rc;
+    if ((rc = alloc(&c->adj_work, 10 * c->field_bytes())) ||
+        (rc = alloc((void**)&c->adj_rows, (size_t)flb::adjoint_rows(c->m) * 6 * sizeof(double))) ||
+        (rc = alloc((void**)&c->adj_col, 8 * sizeof(double))))
+        return rc;
+    FLB_CUDA(flb::adjoint_step(c->m, c->prec, step, g_n, lam_next, lam, c->adj_work, c->adj_rows, c->adj_col, grad,
+                               c->stream));
     return FLB_OK;
 }
 

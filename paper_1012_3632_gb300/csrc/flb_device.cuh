@@ -131,18 +131,87 @@ __device__ __forceinline__ void normals4(const PhiloxKeys& K, uint32_t site, uin
 // ---------------------------------------------------------------------------
 // Collision parameters (per launch, in the kernel's parameter bank)
 // ---------------------------------------------------------------------------
+// Per non-conserved mode k (mode a = D + 1 + k) the kernel adds
+//   (m*_a - m_a) / N_a = frc[k] m^F_a + rel[k] (m_a - m^eq_a) + ns[k] sqrt(rho) z_k
+// with rel = -omega_a / N_a, frc = (1 - omega_a / 2) / N_a (stress modes only; the
+// ghosts have m^eq = m^F = 0) and ns = sqrt(kT omega_a (2 - omega_a) N_a / cs^2) / N_a.
 template <class R>
 struct Coll {
-    R rho0;
-    R om_b, om_s, om_g;   // lattice relaxation rates lambda^LB of bulk, shear, ghost modes
-    R h_b, h_s;           // 1 - omega/2 of the bulk and shear modes (forcing prefactor)
-    R ns[16];             // noise scale of non-conserved mode k: sqrt(kT w (2-w) N_a / cs^2) / N_a
-    R sqrt_rho0;
+    R rho0, sqrt_rho0;
+    R rel[16];
+    R frc[6];
+    R ns[16];
     int noise;            // kT > 0
     int noise_local;      // local rho (1) or rho0 (0) in the noise variance
     PhiloxKeys key;       // Philox round keys
-    uint32_t step, replica;
+    uint32_t step;        // time step keying the noise (single-lattice launches)
+    uint32_t replica;     // fourth Philox counter word
 };
+
+// ---------------------------------------------------------------------------
+// Two lattice sites in one register pair: packed single-precision arithmetic
+// (FADD2 / FMUL2 / FFMA2 of sm_100 and later) for kernels that update sites
+// x and x+1 together.
+// ---------------------------------------------------------------------------
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    __device__ __forceinline__ explicit F2(double c) : v(make_float2((float)c, (float)c)) {}
+    __device__ __forceinline__ explicit F2(float c) : v(make_float2(c, c)) {}
+    __device__ __forceinline__ explicit F2(int c) : v(make_float2((float)c, (float)c)) {}
+};
+__device__ __forceinline__ F2 mk2(float2 v)
+{
+    F2 r;
+    r.v = v;
+    return r;
+}
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return mk2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return mk2(__ffma2_rn(b.v, make_float2(-1.f, -1.f), a.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return mk2(__fmul2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator*(float a, F2 b) { return mk2(__fmul2_rn(make_float2(a, a), b.v)); }
+__device__ __forceinline__ F2 operator*(F2 a, float b) { return mk2(__fmul2_rn(a.v, make_float2(b, b))); }
+__device__ __forceinline__ F2 operator+(float a, F2 b) { return mk2(__fadd2_rn(make_float2(a, a), b.v)); }
+__device__ __forceinline__ F2 operator+(F2 a, float b) { return mk2(__fadd2_rn(a.v, make_float2(b, b))); }
+__device__ __forceinline__ F2& operator+=(F2& a, F2 b)
+{
+    a = a + b;
+    return a;
+}
+__device__ __forceinline__ F2& operator*=(F2& a, F2 b)
+{
+    a = a * b;
+    return a;
+}
+
+// reciprocal and square root: the FP32 paths use the SFU approximations (the
+// density is ~1 and the results feed terms far below FP32 storage rounding)
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ F2 rcp_(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+__device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+__device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ F2 sqrt_(F2 x) { return F2(sqrt_(x.v.x), sqrt_(x.v.y)); }
+
+// Normals 0..N-1 of the collision noise of `site` (one site per lane).
+template <int NCALL, class R>
+__device__ __forceinline__ void noise_normals(const PhiloxKeys& K, uint32_t site, uint32_t step, uint32_t rep,
+                                              R z[4 * NCALL])
+{
+#pragma unroll
+    for (int b = 0; b < NCALL; ++b) normals4(K, site, step, (uint32_t)b, rep, z + 4 * b);
+}
+template <int NCALL>
+__device__ __forceinline__ void noise_normals(const PhiloxKeys& K, uint32_t site, uint32_t step, uint32_t rep,
+                                              F2 z[4 * NCALL])
+{
+    float a[4 * NCALL], b[4 * NCALL];
+    noise_normals<NCALL>(K, site, step, rep, a);
+    noise_normals<NCALL>(K, site + 1, step, rep, b);
+#pragma unroll
+    for (int k = 0; k < 4 * NCALL; ++k) z[k] = F2(a[k], b[k]);
+}
 
 // ---------------------------------------------------------------------------
 // D2Q9 (App. B).  Velocity order: (0,0) (1,0) (0,1) (-1,0) (0,-1) (1,1) (-1,1)
@@ -224,13 +293,14 @@ struct D2Q9 {
     }
 
     // Equilibrium (Eq. (feq)) and forcing (Guo form) moments of the stress modes.
-    template <class R>
-    __device__ __forceinline__ static void collide(R g[9], R Fx, R Fy, const Coll<R>& P, uint32_t site)
+    template <class R, class PR>
+    __device__ __forceinline__ static void collide(R g[9], R Fx, R Fy, const Coll<PR>& P, uint32_t site,
+                                                   uint32_t step)
     {
         R m[9];
         moments(g, m);
         const R rho = P.rho0 + m[0];
-        const R ir = R(1) / rho;
+        const R ir = rcp_(rho);
         const R ux = (m[1] + R(0.5) * Fx) * ir, uy = (m[2] + R(0.5) * Fy) * ir;
         const R uxx = ux * ux, uyy = uy * uy;
         const R eq_e = R(3) * rho * (uxx + uyy);
@@ -243,19 +313,18 @@ struct D2Q9 {
         Dm[0] = R(0);
         Dm[1] = R(3) * Fx;
         Dm[2] = R(3) * Fy;
-        Dm[3] = R(0.25) * (P.h_b * F_e - P.om_b * (m[3] - eq_e));
-        Dm[4] = R(2.25) * (P.h_s * F_w - P.om_s * (m[4] - eq_w));
-        Dm[5] = R(9) * (P.h_s * F_xy - P.om_s * (m[5] - eq_xy));
-        Dm[6] = R(-1.5) * P.om_g * m[6];
-        Dm[7] = R(-1.5) * P.om_g * m[7];
-        Dm[8] = R(-1.0 / 16.0) * P.om_g * m[8];
+        Dm[3] = P.frc[0] * F_e + P.rel[0] * (m[3] - eq_e);
+        Dm[4] = P.frc[1] * F_w + P.rel[1] * (m[4] - eq_w);
+        Dm[5] = P.frc[2] * F_xy + P.rel[2] * (m[5] - eq_xy);
+        Dm[6] = P.rel[3] * m[6];
+        Dm[7] = P.rel[4] * m[7];
+        Dm[8] = P.rel[5] * m[8];
         if (P.noise) {
-            const R sr = P.noise_local ? sqrt(rho) : P.sqrt_rho0;
+            const R sr = P.noise_local ? sqrt_(rho) : R(P.sqrt_rho0);
             R z[8];
-            normals4(P.key, site, P.step, 0u, P.replica, z);
-            normals4(P.key, site, P.step, 1u, P.replica, z + 4);
+            noise_normals<2>(P.key, site, step, P.replica, z);
 #pragma unroll
-            for (int k = 0; k < 6; ++k) Dm[3 + k] += P.ns[k] * sr * z[k];
+            for (int k = 0; k < 6; ++k) Dm[3 + k] += P.ns[k] * (sr * z[k]);
         }
         add_back(Dm, g);
     }
@@ -312,34 +381,37 @@ struct D3Q19 {
         m[18] = R(0.5) * (s3 - s2 + sxy - sxz);
     }
 
-    // g_i += w_i sum_a T_ai D_a over the modes a >= 1.
-    template <class R>
+    // g_i += w_i sum_a T_ai D_a over the modes a >= 1 (J = false: the momentum
+    // increments D_1..3 are zero and skipped).
+    template <bool J = true, class R>
     __device__ __forceinline__ static void add_back(const R Dm[19], R g[19])
     {
         const R De = Dm[4], D5 = Dm[5], D6 = Dm[6], D7 = Dm[7], D8 = Dm[8], D9 = Dm[9];
         const R D10 = Dm[10], D11 = Dm[11], D12 = Dm[12], D13 = Dm[13], D14 = Dm[14], D15 = Dm[15];
         const R D16 = Dm[16], D17 = Dm[17], D18 = Dm[18];
         const R Jx = Dm[1], Jy = Dm[2], Jz = Dm[3];
+        // odd parts without the momentum increments
+        auto odd = [&](R j, R rest) { if constexpr (J) return j + rest; else return rest; };
         const R t16 = R(1.0 / 3.0) * D16, h17 = R(0.5) * D17, h18 = R(0.5) * D18;
         const R a10 = R(1.0 / 3.0) * D10, a11 = R(1.0 / 3.0) * D11, a12 = R(1.0 / 3.0) * D12;
         // rest particle: e = -1, c^4-2c^2+1/3 = 1/3
         g[0] += R(1.0 / 3.0) * (t16 - De);
         // axis pairs: e = 0, c^4-term = -2/3
         const R Ea = R(-2) * t16;
-        const R E1 = Ea + R(2) * D5 - D17, O1 = Jx - R(2) * a10;
-        const R E2 = Ea - D5 + D6 + h17 - h18, O2 = Jy - R(2) * a11;
-        const R E3 = Ea - D5 - D6 + h17 + h18, O3 = Jz - R(2) * a12;
+        const R E1 = Ea + R(2) * D5 - D17, O1 = odd(Jx, R(-2) * a10);
+        const R E2 = Ea - D5 + D6 + h17 - h18, O2 = odd(Jy, R(-2) * a11);
+        const R E3 = Ea - D5 - D6 + h17 + h18, O3 = odd(Jz, R(-2) * a12);
         // edge pairs: e = 1, c^4-term = 1/3
         const R Ee = De + t16;
         const R Exy = Ee + D5 + D6 + h17 + h18;
-        const R E4 = Exy + D7, O4 = Jx + Jy + a10 + a11 + D13 - D14;
-        const R E5 = Exy - D7, O5 = Jx - Jy + a10 - a11 + D13 + D14;
+        const R E4 = Exy + D7, O4 = odd(Jx + Jy, a10 + a11 + D13 - D14);
+        const R E5 = Exy - D7, O5 = odd(Jx - Jy, a10 - a11 + D13 + D14);
         const R Exz = Ee + D5 - D6 + h17 - h18;
-        const R E6 = Exz + D9, O6 = Jx + Jz + a10 + a12 - D13 + D15;
-        const R E7 = Exz - D9, O7 = Jx - Jz + a10 - a12 - D13 - D15;
+        const R E6 = Exz + D9, O6 = odd(Jx + Jz, a10 + a12 - D13 + D15);
+        const R E7 = Exz - D9, O7 = odd(Jx - Jz, a10 - a12 - D13 - D15);
         const R Eyz = Ee - R(2) * D5 - D17;
-        const R E8 = Eyz + D8, O8 = Jy + Jz + a11 + a12 + D14 - D15;
-        const R E9 = Eyz - D8, O9 = Jy - Jz + a11 - a12 + D14 + D15;
+        const R E8 = Eyz + D8, O8 = odd(Jy + Jz, a11 + a12 + D14 - D15);
+        const R E9 = Eyz - D8, O9 = odd(Jy - Jz, a11 - a12 + D14 + D15);
         constexpr double wa = 1.0 / 18.0, we = 1.0 / 36.0;
         g[1] += R(wa) * (E1 + O1);
         g[2] += R(wa) * (E1 - O1);
@@ -395,53 +467,61 @@ struct D3Q19 {
         for (int a = 10; a < 19; ++a) m[a] = R(0);
     }
 
-    template <class R>
-    __device__ __forceinline__ static void collide(R g[19], R Fx, R Fy, R Fz, const Coll<R>& P, uint32_t site)
+    // FORCE = false: F = 0 (ideal gas); the force terms are not evaluated.
+    template <bool FORCE = true, class R, class PR>
+    __device__ __forceinline__ static void collide(R g[19], R Fx, R Fy, R Fz, const Coll<PR>& P, uint32_t site,
+                                                   uint32_t step)
     {
         R m[19];
         moments(g, m);
         const R rho = P.rho0 + m[0];
-        const R ir = R(1) / rho;
-        const R ux = (m[1] + R(0.5) * Fx) * ir;
-        const R uy = (m[2] + R(0.5) * Fy) * ir;
-        const R uz = (m[3] + R(0.5) * Fz) * ir;
+        const R ir = rcp_(rho);
+        R ux, uy, uz;
+        if constexpr (FORCE) {
+            ux = (m[1] + R(0.5) * Fx) * ir;
+            uy = (m[2] + R(0.5) * Fy) * ir;
+            uz = (m[3] + R(0.5) * Fz) * ir;
+        } else {
+            ux = m[1] * ir;
+            uy = m[2] * ir;
+            uz = m[3] * ir;
+        }
         const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz, uu = uxx + uyy + uzz;
-        const R uFx = ux * Fx, uFy = uy * Fy, uFz = uz * Fz, uF = uFx + uFy + uFz;
         R Dm[19];
         Dm[0] = R(0);
-        Dm[1] = R(3) * Fx;
-        Dm[2] = R(3) * Fy;
-        Dm[3] = R(3) * Fz;
         // bulk: m^eq = rho u^2, m^F = 2 u.F
-        Dm[4] = R(1.5) * (P.h_b * R(2) * uF - P.om_b * (m[4] - rho * uu));
         // shear: m^eq = rho(3ux^2-u^2), rho(uy^2-uz^2), rho ux uy, rho uy uz, rho uz ux
-        Dm[5] = R(0.75) * (P.h_s * R(2) * (R(3) * uFx - uF) - P.om_s * (m[5] - rho * (R(3) * uxx - uu)));
-        Dm[6] = R(2.25) * (P.h_s * R(2) * (uFy - uFz) - P.om_s * (m[6] - rho * (uyy - uzz)));
-        Dm[7] = R(9) * (P.h_s * (ux * Fy + uy * Fx) - P.om_s * (m[7] - rho * ux * uy));
-        Dm[8] = R(9) * (P.h_s * (uy * Fz + uz * Fy) - P.om_s * (m[8] - rho * uy * uz));
-        Dm[9] = R(9) * (P.h_s * (uz * Fx + ux * Fz) - P.om_s * (m[9] - rho * uz * ux));
-        // ghosts relax to 0
-        const R og = P.om_g;
-        Dm[10] = R(-13.5) * og * m[10];
-        Dm[11] = R(-13.5) * og * m[11];
-        Dm[12] = R(-13.5) * og * m[12];
-        Dm[13] = R(-4.5) * og * m[13];
-        Dm[14] = R(-4.5) * og * m[14];
-        Dm[15] = R(-4.5) * og * m[15];
-        Dm[16] = R(-4.5) * og * m[16];
-        Dm[17] = R(-3) * og * m[17];
-        Dm[18] = R(-9) * og * m[18];
-        if (P.noise) {
-            const R sr = P.noise_local ? sqrt(rho) : P.sqrt_rho0;
-            R z[16];
-            normals4(P.key, site, P.step, 0u, P.replica, z);
-            normals4(P.key, site, P.step, 1u, P.replica, z + 4);
-            normals4(P.key, site, P.step, 2u, P.replica, z + 8);
-            normals4(P.key, site, P.step, 3u, P.replica, z + 12);
-#pragma unroll
-            for (int k = 0; k < 15; ++k) Dm[4 + k] += P.ns[k] * sr * z[k];
+        Dm[4] = P.rel[0] * (m[4] - rho * uu);
+        Dm[5] = P.rel[1] * (m[5] - rho * (R(3) * uxx - uu));
+        Dm[6] = P.rel[2] * (m[6] - rho * (uyy - uzz));
+        Dm[7] = P.rel[3] * (m[7] - rho * (ux * uy));
+        Dm[8] = P.rel[4] * (m[8] - rho * (uy * uz));
+        Dm[9] = P.rel[5] * (m[9] - rho * (uz * ux));
+        if constexpr (FORCE) {
+            const R uFx = ux * Fx, uFy = uy * Fy, uFz = uz * Fz, uF = uFx + uFy + uFz;
+            Dm[1] = R(3) * Fx;
+            Dm[2] = R(3) * Fy;
+            Dm[3] = R(3) * Fz;
+            Dm[4] += P.frc[0] * (R(2) * uF);
+            Dm[5] += P.frc[1] * (R(2) * (R(3) * uFx - uF));
+            Dm[6] += P.frc[2] * (R(2) * (uFy - uFz));
+            Dm[7] += P.frc[3] * (ux * Fy + uy * Fx);
+            Dm[8] += P.frc[4] * (uy * Fz + uz * Fy);
+            Dm[9] += P.frc[5] * (uz * Fx + ux * Fz);
+        } else {
+            Dm[1] = Dm[2] = Dm[3] = R(0);
         }
-        add_back(Dm, g);
+        // ghosts relax to 0
+#pragma unroll
+        for (int a = 10; a < 19; ++a) Dm[a] = P.rel[a - 4] * m[a];
+        if (P.noise) {
+            const R sr = P.noise_local ? sqrt_(rho) : R(P.sqrt_rho0);
+            R z[16];
+            noise_normals<4>(P.key, site, step, P.replica, z);
+#pragma unroll
+            for (int k = 0; k < 15; ++k) Dm[4 + k] += P.ns[k] * (sr * z[k]);
+        }
+        add_back<FORCE>(Dm, g);
     }
 };
 

@@ -3,4 +3,5 @@
 
 namespace flb {
 const PrecOps& ops_fp64() { return Prec<double, double>::ops(); }
+Coll<double> coll_fp64(const HostModel& m, uint64_t step) { return make_coll<D3Q19, double>(m, step); }
 }  // namespace flb

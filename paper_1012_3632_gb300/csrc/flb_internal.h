@@ -48,6 +48,9 @@ struct PrecOps {
     cudaError_t (*mode_field)(const HostModel&, const void* src, int mode, double2* out, cudaStream_t);
     int (*partial_rows_max)(const HostModel&);
     int (*step_needs_density)(const HostModel&);
+    // pre-collision deviations in the storage type, [i][s], to / from a device buffer
+    cudaError_t (*pull_state)(const HostModel&, const void* src, void* out, cudaStream_t);
+    cudaError_t (*push_state)(const HostModel&, const void* in, void* dst, cudaStream_t);
 };
 
 const PrecOps& ops_fp64();
@@ -66,6 +69,14 @@ int set_error(int code, const std::string& msg);
 
 // In-place forward DFT along every axis of length > 1 of a complex X*Y*Z field.
 cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s);
+
+// Adjoint of one D3Q19 step (flb_adjoint.cu): gn, lam_next, lam are [19][V]
+// pre-collision deviations / adjoints in the storage type (FP64 or FP32);
+// work holds 10 V compute-type scalars, rows adjoint_rows(m) * 6 doubles,
+// colsum 6 doubles; grad (6 doubles) is incremented.
+cudaError_t adjoint_step(const HostModel& m, int prec, uint64_t step, const void* gn, const void* lam_next, void* lam,
+                         void* work, double* rows, double* colsum, double* grad, cudaStream_t st);
+int adjoint_rows(const HostModel& m);
 
 // p = |data|^2 / V with p(0) = 0; accumulate: acc += p, else out = p.
 cudaError_t power_spectrum(const double2* data, long V, double* acc, double* out, cudaStream_t s);

@@ -218,11 +218,83 @@ __global__ void __launch_bounds__(TX* TY* TZ)
     pull_planes<L, false>(P, nb, g);
     const int s = x + X * (y + Y * z);
     if constexpr (L::D == 3)
-        L::collide(g, F[0], F[1], F[2], a.c, (uint32_t)s);
+        L::template collide<NONIDEAL>(g, F[0], F[1], F[2], a.c, (uint32_t)s, a.c.step);
     else
-        L::collide(g, F[0], F[1], a.c, (uint32_t)s);
+        L::collide(g, F[0], F[1], a.c, (uint32_t)s, a.c.step);
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) store_stream(P.dst[i] + s, g[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Ideal gas, FP32 storage, two sites (x, x+1) per thread with packed FP32
+// arithmetic (F2).  X must be even: a thread's pair then never straddles a row
+// and its populations at (x, x+1) are 8-byte aligned.  Pulls along c_x = 0 are
+// single 8-byte loads; along c_x = +-1 the pair comes from (x-1, x) or
+// (x+1, x+2).  Block = TXT x TY x TZ threads covering 2 TXT x TY x TZ sites.
+// ---------------------------------------------------------------------------
+template <class L, int TXT, int TY, int TZ>
+__global__ void __launch_bounds__(TXT* TY* TZ)
+    k_step2(const StepArgs<float> a, const __grid_constant__ Planes<float> P)
+{
+    const int x = 2 * (blockIdx.x * TXT + threadIdx.x);
+    const int y = blockIdx.y * TY + threadIdx.y;
+    const int z = blockIdx.z * TZ + threadIdx.z;
+    const int X = a.X, Y = a.Y, Z = a.Z;
+    if (x >= X || y >= Y || z >= Z) return;
+    const int xm = x == 0 ? X - 1 : x - 1;  // x - 1
+    const int x2 = x + 2 == X ? 0 : x + 2;  // x + 2
+    const int yv[3] = {wrap_once(y - 1, Y), y, wrap_once(y + 1, Y)};
+    const int zv[3] = {wrap_once(z - 1, Z), z, wrap_once(z + 1, Z)};
+    int rb[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) rb[i][j] = X * (yv[i] + Y * zv[j]);
+    F2 g[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const float* p = P.src[i] + rb[1 - Vel<L>::cy(i)][1 - Vel<L>::cz(i)];
+        const int cx = Vel<L>::cx(i);
+        if (cx == 0)
+            g[i] = mk2(*reinterpret_cast<const float2*>(p + x));
+        else if (cx > 0)
+            g[i] = F2(p[xm], p[x]);
+        else
+            g[i] = F2(p[x + 1], p[x2]);
+    }
+    const int s = x + X * (y + Y * z);
+    L::template collide<false>(g, F2(0.f), F2(0.f), F2(0.f), a.c, (uint32_t)s, a.c.step);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) __stcs(reinterpret_cast<float2*>(P.dst[i] + s), g[i].v);
+}
+
+// Density gather for site pairs (x, x+1), packed FP32; X even.
+template <int TXT, int TY, int TZ>
+__global__ void __launch_bounds__(TXT* TY* TZ)
+    k_density2(const __grid_constant__ Planes<float> P, float* __restrict__ drho, int X, int Y, int Z)
+{
+    using L = D3Q19;
+    const int x = 2 * (blockIdx.x * TXT + threadIdx.x);
+    const int y = blockIdx.y * TY + threadIdx.y;
+    const int z = blockIdx.z * TZ + threadIdx.z;
+    if (x >= X || y >= Y || z >= Z) return;
+    const int xm = x == 0 ? X - 1 : x - 1, x2 = x + 2 == X ? 0 : x + 2;
+    const int yv[3] = {wrap_once(y - 1, Y), y, wrap_once(y + 1, Y)};
+    const int zv[3] = {wrap_once(z - 1, Z), z, wrap_once(z + 1, Z)};
+    F2 g[L::Q], m[L::Q];
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) {
+        const float* p = P.src[i] + X * (yv[1 - Vel<L>::cy(i)] + Y * zv[1 - Vel<L>::cz(i)]);
+        const int cx = Vel<L>::cx(i);
+        if (cx == 0)
+            g[i] = mk2(*reinterpret_cast<const float2*>(p + x));
+        else if (cx > 0)
+            g[i] = F2(p[xm], p[x]);
+        else
+            g[i] = F2(p[x + 1], p[x2]);
+    }
+    L::moments(g, m);
+    *reinterpret_cast<float2*>(drho + x + X * (y + Y * z)) = m[0].v;
 }
 
 // ---------------------------------------------------------------------------
@@ -266,16 +338,32 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         hy[h][2] = X * wrap_once(gy + 1, Y);
     }
 
+    // this thread's chemical-potential sites: centre offset in the density plane
+    constexpr int NMU = (MP + NT - 1) / NT;
+    int mc[NMU];
+#pragma unroll
+    for (int j = 0; j < NMU; ++j) {
+        const int e = min(tid + j * NT, MP - 1);
+        mc[j] = (e % MX + 1) + RX * (e / MX + 1);
+    }
+
     const int x = xb + threadIdx.x, y = yb + threadIdx.y;
     const int cm = (threadIdx.x + 1) + MX * (threadIdx.y + 1);
     const int cr = (threadIdx.x + 2) + RX * (threadIdx.y + 2);
+    // ring slots, advanced by one each iteration: plane zb+k+2 of the density
+    // goes to slot (k+4) mod 5 = ra + 2, the collision reads density slot
+    // ra = (k+2) mod 5 and chemical-potential slots (k, k+1, k+2) mod 3.
+    int ra = 3;       // (k + 2) mod 5 at k = -4
+    int mb = 2;       // k mod 3 at k = -4
+    int zc = wrap_any(zb - 2, Z);  // density plane being gathered, wrapped
 #pragma unroll 1
     for (int k = -4; k < nz; ++k) {
+        const int ra1 = ra == 4 ? 0 : ra + 1, ra2 = ra1 == 4 ? 0 : ra1 + 1;
+        const int mb1 = mb == 2 ? 0 : mb + 1, mb2 = mb1 == 2 ? 0 : mb1 + 1;
         // (1) density of plane zb+k+2 on the tile + 2 halo: drho = sum_i g*_i(r - c_i)
         {
-            const int zc = wrap_any(zb + k + 2, Z);
-            const int zo[3] = {XY * wrap_once(zc - 1, Z), XY * zc, XY * wrap_once(zc + 1, Z)};
-            R* out = srho[(k + 4) % 5];
+            const int zo[3] = {XY * (zc == 0 ? Z - 1 : zc - 1), XY * zc, XY * (zc == Z - 1 ? 0 : zc + 1)};
+            R* out = srho[ra2];
 #pragma unroll
             for (int h = 0; h < NRH; ++h) {
                 const int e = tid + h * NT;
@@ -293,32 +381,36 @@ __global__ void __launch_bounds__(TX* TY, MINB)
         __syncthreads();
         // (2) mu = psi'(rho) - kappa lap rho of plane zb+k+1 on the tile + 1 halo
         if (k >= -2) {
-            const R* rm = srho[(k + 2) % 5];
-            const R* r0 = srho[(k + 3) % 5];
-            const R* rp = srho[(k + 4) % 5];
-            R* out = smu[(k + 2) % 3];
-            for (int e = tid; e < MP; e += NT) {
-                const int c = (e % MX + 1) + RX * (e / MX + 1);
-                const R rc = r0[c];
-                R lap = R(0);
+            const R* rm = srho[ra];
+            const R* r0 = srho[ra1];
+            const R* rp = srho[ra2];
+            R* out = smu[mb2];
 #pragma unroll
-                for (int i = 1; i < L::Q; ++i) {
-                    const int cz = Vel<L>::cz(i);
-                    const R* pl = cz > 0 ? rp : (cz < 0 ? rm : r0);
-                    lap += R(Vel<L>::w(i)) * (pl[c + Vel<L>::cx(i) + RX * Vel<L>::cy(i)] - rc);
+            for (int j = 0; j < NMU; ++j) {
+                const int e = tid + j * NT;
+                if (e < MP) {
+                    const int c = mc[j];
+                    const R rc = r0[c];
+                    R lap = R(0);
+#pragma unroll
+                    for (int i = 1; i < L::Q; ++i) {
+                        const int cz = Vel<L>::cz(i);
+                        const R* pl = cz > 0 ? rp : (cz < 0 ? rm : r0);
+                        lap += R(Vel<L>::w(i)) * (pl[c + Vel<L>::cx(i) + RX * Vel<L>::cy(i)] - rc);
+                    }
+                    lap *= R(6);
+                    const R d = rc + a.rho0_minus_rhoc;
+                    out[e] = d * (a.A + a.B * d * d) - a.kappa * lap;
                 }
-                lap *= R(6);
-                const R d = rc + a.rho0_minus_rhoc;
-                out[e] = d * (a.A + a.B * d * d) - a.kappa * lap;
             }
         }
         __syncthreads();
         // (3) collide plane zb+k with F = -rho grad mu, grad = 3 sum_i w_i c_i mu(r + c_i)
         if (k >= 0 && x < X && y < Y) {
             const int z = zb + k;
-            const R* mlo = smu[k % 3];
-            const R* mmid = smu[(k + 1) % 3];
-            const R* mhi = smu[(k + 2) % 3];
+            const R* mlo = smu[mb];
+            const R* mmid = smu[mb1];
+            const R* mhi = smu[mb2];
             R gx = R(0), gy = R(0), gz = R(0);
 #pragma unroll
             for (int i = 1; i < L::Q; ++i) {
@@ -329,15 +421,194 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                 if (Vel<L>::cy(i)) gy += R(Vel<L>::cy(i)) * wm;
                 if (Vel<L>::cz(i)) gz += R(Vel<L>::cz(i)) * wm;
             }
-            const R pre = R(-3) * (a.c.rho0 + srho[(k + 2) % 5][cr]);
+            const R pre = R(-3) * (a.c.rho0 + srho[ra][cr]);
             const Nbhd nb(x, y, z, X, Y, Z);
             R g[L::Q];
             pull_planes<L, true>(P, nb, g);
             const int s = x + X * (y + Y * z);
-            L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s);
+            L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) store_stream(P.dst[i] + s, g[i]);
         }
+        ra = ra1;
+        mb = mb1;
+        zc = zc == Z - 1 ? 0 : zc + 1;
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// Packed-FP32 form of k_step_march: each thread owns the two sites (x, x+1)
+// of its column pair, and every stage (density gather, mu, F, collision) works
+// on site pairs with FADD2/FMUL2/FFMA2.  X must be even.  Same algorithm and
+// ring layout as k_step_march; the density and mu planes are stored as float2
+// pairs.
+// ---------------------------------------------------------------------------
+template <int TXT, int TY, int NZ, int MINB, bool GATHER = true>
+__global__ void __launch_bounds__(TXT* TY, MINB)
+    k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<float> P, const float* __restrict__ drho)
+{
+    using L = D3Q19;
+    constexpr int NT = TXT * TY;
+    constexpr int RXP = TXT + 2, RY = TY + 4, RPP = RXP * RY;  // density pairs per plane (tile + 2 halo)
+    constexpr int MXP = TXT + 1, MY = TY + 2, MPP = MXP * MY;  // mu pairs per plane (tile + 1 halo)
+    constexpr int RX = 2 * RXP, MX = 2 * MXP;                  // floats per row
+    __shared__ __align__(16) float srho[5][RPP * 2];
+    __shared__ __align__(16) float smu[3][MPP * 2];
+    const int tid = threadIdx.x + TXT * threadIdx.y;
+    const int X = a.X, Y = a.Y, Z = a.Z;
+    const int XY = X * Y;
+    const int xb = blockIdx.x * 2 * TXT, yb = blockIdx.y * TY, zb = blockIdx.z * NZ;
+    const int nz = min(NZ, Z - zb);
+    const bool small = X < RX || Y < RY;
+
+    // density pairs of this thread: first site x (even), x-1, x+2 and rows
+    constexpr int NRH = (RPP + NT - 1) / NT;
+    int hx[NRH][3], hy[NRH][3];
+#pragma unroll
+    for (int h = 0; h < NRH; ++h) {
+        const int e = min(tid + h * NT, RPP - 1);
+        const int gx = small ? wrap_any(xb - 2 + 2 * (e % RXP), X) : wrap_once(xb - 2 + 2 * (e % RXP), X);
+        const int gy = small ? wrap_any(yb - 2 + e / RXP, Y) : wrap_once(yb - 2 + e / RXP, Y);
+        hx[h][0] = gx == 0 ? X - 1 : gx - 1;
+        hx[h][1] = gx;
+        hx[h][2] = gx + 2 == X ? 0 : gx + 2;
+        hy[h][0] = X * wrap_once(gy - 1, Y);
+        hy[h][1] = X * gy;
+        hy[h][2] = X * wrap_once(gy + 1, Y);
+    }
+    constexpr int NMU = (MPP + NT - 1) / NT;
+    int mc[NMU];  // float offset of the first site of a mu pair in the density plane
+#pragma unroll
+    for (int j = 0; j < NMU; ++j) {
+        const int e = min(tid + j * NT, MPP - 1);
+        mc[j] = 2 * (e % MXP) + 1 + RX * (e / MXP + 1);
+    }
+
+    const int x = xb + 2 * threadIdx.x, y = yb + threadIdx.y;
+    const int cm = 2 * threadIdx.x + 1 + MX * (threadIdx.y + 1);  // first site in the mu plane
+    const int cr = 2 * threadIdx.x + 2 + RX * (threadIdx.y + 2);  // first site in the density plane
+    int ra = 3, mb = 2;
+    int zc = wrap_any(zb - 2, Z);
+    // pair at float offset o of a plane: aligned 8-byte read when o is even
+    auto pair_at = [](const float* pl, int o, int cx) -> F2 {
+        if (cx == 0) return mk2(*reinterpret_cast<const float2*>(pl + o));
+        return F2(pl[o], pl[o + 1]);
+    };
+#pragma unroll 1
+    for (int k = -4; k < nz; ++k) {
+        const int ra1 = ra == 4 ? 0 : ra + 1, ra2 = ra1 == 4 ? 0 : ra1 + 1;
+        const int mb1 = mb == 2 ? 0 : mb + 1, mb2 = mb1 == 2 ? 0 : mb1 + 1;
+        // (1) density pairs of plane zb+k+2, tile + 2 halo
+        {
+            const int zo[3] = {XY * (zc == 0 ? Z - 1 : zc - 1), XY * zc, XY * (zc == Z - 1 ? 0 : zc + 1)};
+            float* out = srho[ra2];
+#pragma unroll
+            for (int h = 0; h < NRH; ++h) {
+                const int e = tid + h * NT;
+                if (e < RPP) {
+                    if constexpr (GATHER) {
+                        F2 g[L::Q], m[L::Q];
+#pragma unroll
+                        for (int i = 0; i < L::Q; ++i) {
+                            const float* p = P.src[i] + hy[h][1 - Vel<L>::cy(i)] + zo[1 - Vel<L>::cz(i)];
+                            const int cx = Vel<L>::cx(i);
+                            if (cx == 0)
+                                g[i] = mk2(*reinterpret_cast<const float2*>(p + hx[h][1]));
+                            else if (cx > 0)
+                                g[i] = F2(p[hx[h][0]], p[hx[h][1]]);
+                            else
+                                g[i] = F2(p[hx[h][1] + 1], p[hx[h][2]]);
+                        }
+                        L::moments(g, m);
+                        *reinterpret_cast<float2*>(out + 2 * e) = m[0].v;
+                    } else {
+                        // density written by the gather kernel of this step
+                        *reinterpret_cast<float2*>(out + 2 * e) =
+                            *reinterpret_cast<const float2*>(drho + hx[h][1] + hy[h][1] + zo[1]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // (2) mu pairs of plane zb+k+1, tile + 1 halo
+        if (k >= -2) {
+            const float* rm = srho[ra];
+            const float* r0 = srho[ra1];
+            const float* rp = srho[ra2];
+            float* out = smu[mb2];
+#pragma unroll
+            for (int j = 0; j < NMU; ++j) {
+                const int e = tid + j * NT;
+                if (e < MPP) {
+                    const int c = mc[j];
+                    const F2 rc = F2(r0[c], r0[c + 1]);
+                    F2 lap(0.f);
+#pragma unroll
+                    for (int i = 1; i < L::Q; ++i) {
+                        const int cz = Vel<L>::cz(i);
+                        const float* pl = cz > 0 ? rp : (cz < 0 ? rm : r0);
+                        // c is odd: pairs at c + cx are aligned only for cx = +-1
+                        const int o = c + Vel<L>::cx(i) + RX * Vel<L>::cy(i);
+                        const F2 v = Vel<L>::cx(i) != 0 ? mk2(*reinterpret_cast<const float2*>(pl + o))
+                                                        : F2(pl[o], pl[o + 1]);
+                        lap += (float)Vel<L>::w(i) * (v - rc);
+                    }
+                    const F2 d = rc + a.rho0_minus_rhoc;
+                    const F2 mu = d * (a.A + a.B * (d * d)) - (6.0f * a.kappa) * lap;
+                    out[2 * e] = mu.v.x;
+                    out[2 * e + 1] = mu.v.y;
+                }
+            }
+        }
+        __syncthreads();
+        // (3) collide the pair of plane zb+k with F = -rho grad mu
+        if (k >= 0 && x < X && y < Y) {
+            const int z = zb + k;
+            const float* mlo = smu[mb];
+            const float* mmid = smu[mb1];
+            const float* mhi = smu[mb2];
+            F2 gx(0.f), gy(0.f), gz(0.f);
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const int cz = Vel<L>::cz(i);
+                const float* pl = cz > 0 ? mhi : (cz < 0 ? mlo : mmid);
+                const int o = cm + Vel<L>::cx(i) + MX * Vel<L>::cy(i);
+                const F2 v = Vel<L>::cx(i) != 0 ? mk2(*reinterpret_cast<const float2*>(pl + o)) : F2(pl[o], pl[o + 1]);
+                const F2 wm = (float)Vel<L>::w(i) * v;
+                if (Vel<L>::cx(i) > 0) gx += wm;
+                if (Vel<L>::cx(i) < 0) gx = gx - wm;
+                if (Vel<L>::cy(i) > 0) gy += wm;
+                if (Vel<L>::cy(i) < 0) gy = gy - wm;
+                if (Vel<L>::cz(i) > 0) gz += wm;
+                if (Vel<L>::cz(i) < 0) gz = gz - wm;
+            }
+            const F2 rho = a.c.rho0 + mk2(*reinterpret_cast<const float2*>(srho[ra] + cr));
+            const F2 pre = -3.0f * rho;
+            // pull the pair (last read of these populations in this step)
+            const int xm = x == 0 ? X - 1 : x - 1, x2 = x + 2 == X ? 0 : x + 2;
+            const int yv[3] = {wrap_once(y - 1, Y), y, wrap_once(y + 1, Y)};
+            const int zv[3] = {XY * wrap_once(z - 1, Z), XY * z, XY * wrap_once(z + 1, Z)};
+            F2 g[L::Q];
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) {
+                const float* p = P.src[i] + X * yv[1 - Vel<L>::cy(i)] + zv[1 - Vel<L>::cz(i)];
+                const int cx = Vel<L>::cx(i);
+                if (cx == 0)
+                    g[i] = mk2(__ldlu(reinterpret_cast<const float2*>(p + x)));
+                else if (cx > 0)
+                    g[i] = F2(__ldlu(p + xm), __ldlu(p + x));
+                else
+                    g[i] = F2(__ldlu(p + x + 1), __ldlu(p + x2));
+            }
+            const int s = x + X * y + XY * z;
+            L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
+#pragma unroll
+            for (int i = 0; i < L::Q; ++i) __stcs(reinterpret_cast<float2*>(P.dst[i] + s), g[i].v);
+        }
+        ra = ra1;
+        mb = mb1;
+        zc = zc == Z - 1 ? 0 : zc + 1;
     }
 }
 

@@ -5,6 +5,7 @@
 #pragma once
 
 #include <cmath>
+#include <type_traits>
 
 #include "flb_internal.h"
 #include "flb_kernels.cuh"
@@ -13,7 +14,22 @@
 #define FLB_MARCH_MINB 3
 #endif
 #ifndef FLB_MARCH_NZ
-#define FLB_MARCH_NZ 32
+#define FLB_MARCH_NZ 16
+#endif
+#ifndef FLB_MARCH_TY
+#define FLB_MARCH_TY 8
+#endif
+#ifndef FLB_PACKED
+#define FLB_PACKED 1
+#endif
+#ifndef FLB_MARCH2_MINB
+#define FLB_MARCH2_MINB 4
+#endif
+#ifndef FLB_MARCH2_TY
+#define FLB_MARCH2_TY 8
+#endif
+#ifndef FLB_NI_SPLIT
+#define FLB_NI_SPLIT 0
 #endif
 
 namespace flb {
@@ -26,17 +42,17 @@ Coll<R> make_coll(const HostModel& m, uint64_t step)
 {
     Coll<R> c{};
     c.rho0 = R(m.rho0);
-    c.om_b = R(m.om_b);
-    c.om_s = R(m.om_s);
-    c.om_g = R(m.om_g);
-    c.h_b = R(1.0 - 0.5 * m.om_b);
-    c.h_s = R(1.0 - 0.5 * m.om_s);
-    // Eq. (noise-lbe): variance rho kT (2 - w) w N_a / cs^2 added to mode a;
+    // Eq. (lbe-mom) per non-conserved mode a = D + 1 + k, divided by N_a:
+    // relaxation omega_a / N_a, forcing prefactor (1 - omega_a / 2) / N_a, and
+    // Eq. (noise-lbe): variance rho kT (2 - w) w N_a / cs^2 added to m_a, so
     // the kernel adds ns * sqrt(rho) * z to m_a / N_a.
+    const int nstress = L::D * (L::D + 1) / 2;
     for (int k = 0; k < L::NNC; ++k) {
         const int a = L::D + 1 + k;
-        const double om = (a == L::D + 1) ? m.om_b : (a < L::D + 1 + L::D * (L::D + 1) / 2) ? m.om_s : m.om_g;
+        const double om = (k == 0) ? m.om_b : (k < nstress) ? m.om_s : m.om_g;
         const double Na = L::N(a);
+        c.rel[k] = R(-om / Na);
+        if (k < nstress) c.frc[k] = R((1.0 - 0.5 * om) / Na);
         c.ns[k] = R(std::sqrt(m.kT * (2.0 - om) * om * Na * 3.0) / Na);
     }
     c.sqrt_rho0 = R(std::sqrt(m.rho0));
@@ -152,6 +168,37 @@ __global__ void k_set_pop(const double* __restrict__ in, S* __restrict__ dst, do
     for (int i = 0; i < L::Q; ++i)
         store_s(dst + (long)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i)),
                 R(in[(long)i * V + s] - Vel<L>::w(i) * rho0));
+}
+
+// Pre-collision deviations in the storage type, [i][s] (pull of the stored
+// post-collision buffer) and the inverse scatter.
+template <class L, class S>
+__global__ void k_pull_state(const S* __restrict__ src, S* __restrict__ out, int X, int Y, int Z)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z * blockDim.z + threadIdx.z;
+    if (x >= X || y >= Y || z >= Z) return;
+    const long V = (long)X * Y * Z;
+    const int s = x + X * (y + Y * z);
+    const Nbhd nb(x, y, z, X, Y, Z);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+        out[(long)i * V + s] = src[(long)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i))];
+}
+template <class L, class S>
+__global__ void k_push_state(const S* __restrict__ in, S* __restrict__ dst, int X, int Y, int Z)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z * blockDim.z + threadIdx.z;
+    if (x >= X || y >= Y || z >= Z) return;
+    const long V = (long)X * Y * Z;
+    const int s = x + X * (y + Y * z);
+    const Nbhd nb(x, y, z, X, Y, Z);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+        dst[(long)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i))] = in[(long)i * V + s];
 }
 
 // which: 0 rho, 1 u = (j + F/2)/rho, 2 all moments (m_0 = rho).
@@ -333,6 +380,16 @@ struct Prec {
     }
     static cudaError_t density(const HostModel& m, const void* pop, void* drho, cudaStream_t st)
     {
+        if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+            if (m.Q == 19 && m.X % 2 == 0 && FLB_PACKED) {
+                constexpr int TXT = 16, TY = 4, TZ = 2;
+                const dim3 b(TXT, TY, TZ);
+                const dim3 g((m.X / 2 + TXT - 1) / TXT, (m.Y + TY - 1) / TY, (m.Z + TZ - 1) / TZ);
+                k_density2<TXT, TY, TZ><<<g, b, 0, st>>>(make_planes<S>(pop, nullptr, 19, m.V), (float*)drho, m.X,
+                                                          m.Y, m.Z);
+                return cudaGetLastError();
+            }
+        }
         return m.Q == 19 ? density_l<D3Q19>(m, pop, drho, st) : density_l<D2Q9>(m, pop, drho, st);
     }
 
@@ -351,13 +408,38 @@ struct Prec {
     {
         if (m.Q == 19) {
             if (m.nonideal) {
-                constexpr int TX = 32, TY = 8, NZ = FLB_MARCH_NZ;
+                if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+                    if (m.X % 2 == 0 && FLB_PACKED) {
+                        constexpr int TXT = 16, TY = FLB_MARCH2_TY, NZ = FLB_MARCH_NZ;
+                        const StepArgs<R> a = make_args<D3Q19, R>(m, t);
+                        const dim3 b(TXT, TY, 1);
+                        const dim3 g((m.X + 2 * TXT - 1) / (2 * TXT), (m.Y + TY - 1) / TY, (m.Z + NZ - 1) / NZ);
+                        if (FLB_NI_SPLIT)
+                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, false>
+                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V), (const float*)drho);
+                        else
+                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, true>
+                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V), nullptr);
+                        return cudaGetLastError();
+                    }
+                }
+                constexpr int TX = 32, TY = FLB_MARCH_TY, NZ = FLB_MARCH_NZ;
                 const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                 const dim3 b(TX, TY, 1);
                 const dim3 g((m.X + TX - 1) / TX, (m.Y + TY - 1) / TY, (m.Z + NZ - 1) / NZ);
                 k_step_march<R, S, TX, TY, NZ, (sizeof(R) == 8 ? 1 : FLB_MARCH_MINB)>
                     <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                 return cudaGetLastError();
+            }
+            if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+                if (m.X % 2 == 0 && FLB_PACKED) {
+                    constexpr int TXT = 16, TY = 4, TZ = 2;
+                    const StepArgs<R> a = make_args<D3Q19, R>(m, t);
+                    const dim3 b(TXT, TY, TZ);
+                    const dim3 g((m.X / 2 + TXT - 1) / TXT, (m.Y + TY - 1) / TY, (m.Z + TZ - 1) / TZ);
+                    k_step2<D3Q19, TXT, TY, TZ><<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
+                    return cudaGetLastError();
+                }
             }
             return step_t<D3Q19, false, 32, 4, 2>(m, t, src, dst, drho, st);
         }
@@ -433,7 +515,16 @@ struct Prec {
     }
     // The D2Q9 non-ideal step reads a density field gathered beforehand; the
     // D3Q19 one gathers the density itself.
-    static int needs_density(const HostModel& m) { return m.nonideal && m.Q == 9; }
+    static int needs_density(const HostModel& m)
+    {
+        if (!m.nonideal) return 0;
+        if (m.Q == 9) return 1;
+        // packed FP32 D3Q19 with the split gather: the step reads the density field
+        return (std::is_same<R, float>::value && std::is_same<S, float>::value && m.X % 2 == 0 && FLB_PACKED &&
+                FLB_NI_SPLIT)
+                   ? 1
+                   : 0;
+    }
     static int rows(const HostModel& m)
     {
         const dim3 b = m.Q == 19 ? site_block<D3Q19>() : site_block<D2Q9>();
@@ -478,10 +569,34 @@ struct Prec {
         return cudaGetLastError();
     }
 
+    static cudaError_t pull_state(const HostModel& m, const void* src, void* out, cudaStream_t st)
+    {
+        if (m.Q == 19) {
+            const dim3 b = site_block<D3Q19>();
+            k_pull_state<D3Q19, S><<<grid_for(m, b), b, 0, st>>>((const S*)src, (S*)out, m.X, m.Y, m.Z);
+        } else {
+            const dim3 b = site_block<D2Q9>();
+            k_pull_state<D2Q9, S><<<grid_for(m, b), b, 0, st>>>((const S*)src, (S*)out, m.X, m.Y, m.Z);
+        }
+        return cudaGetLastError();
+    }
+    static cudaError_t push_state(const HostModel& m, const void* in, void* dst, cudaStream_t st)
+    {
+        if (m.Q == 19) {
+            const dim3 b = site_block<D3Q19>();
+            k_push_state<D3Q19, S><<<grid_for(m, b), b, 0, st>>>((const S*)in, (S*)dst, m.X, m.Y, m.Z);
+        } else {
+            const dim3 b = site_block<D2Q9>();
+            k_push_state<D2Q9, S><<<grid_for(m, b), b, 0, st>>>((const S*)in, (S*)dst, m.X, m.Y, m.Z);
+        }
+        return cudaGetLastError();
+    }
+
     static const PrecOps& ops()
     {
         static const PrecOps o = {(int)sizeof(S), (int)sizeof(R), density, step, init, get_pop, set_pop, moments,
-                                  mu_force, mode_partials, cons_partials, mode_field, rows, needs_density};
+                                  mu_force, mode_partials, cons_partials, mode_field, rows, needs_density,
+                                  pull_state, push_state};
         return o;
     }
 };

@@ -32,7 +32,11 @@ EXPORTS = [
     "flb_set_populations", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
     "flb_get_info", "flb_kernel_timing", "flb_kernel_times", "flb_save", "flb_load", "flb_error_string",
     "flb_last_error", "flb_destroy", "flb_structure_factor_noalloc",
+    "flb_batch_create", "flb_batch_init", "flb_batch_step", "flb_batch_autotune", "flb_batch_mode_variance",
+    "flb_batch_structure_factor", "flb_batch_get_populations", "flb_batch_info", "flb_batch_synchronize",
+    "flb_batch_destroy", "flb_get_state_device", "flb_set_state_device", "flb_adjoint_step",
 ]
+BATCH_MAX = 96
 NOALLOC_MAX_SITES = 1 << 20
 
 
@@ -91,6 +95,20 @@ def lib():
         "flb_last_error": (ctypes.c_char_p, []),
         "flb_destroy": (None, [vp]),
         "flb_structure_factor_noalloc": (ctypes.c_int, [ctypes.c_int, ip, vp, ctypes.c_int, vp, vp]),
+        "flb_batch_create": (ctypes.c_int, [P(vp), ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp,
+                                            P(ctypes.c_uint64), P(Options)]),
+        "flb_batch_init": (ctypes.c_int, [vp, ctypes.c_int]),
+        "flb_batch_step": (ctypes.c_int, [vp, ctypes.c_int]),
+        "flb_batch_autotune": (ctypes.c_int, [vp, ip]),
+        "flb_batch_mode_variance": (ctypes.c_int, [vp, dp]),
+        "flb_batch_structure_factor": (ctypes.c_int, [vp, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int]),
+        "flb_batch_get_populations": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "flb_batch_info": (ctypes.c_int, [vp, ip, P(ctypes.c_longlong), P(ctypes.c_uint64)]),
+        "flb_batch_synchronize": (ctypes.c_int, [vp]),
+        "flb_batch_destroy": (None, [vp]),
+        "flb_get_state_device": (ctypes.c_int, [vp, vp]),
+        "flb_set_state_device": (ctypes.c_int, [vp, vp]),
+        "flb_adjoint_step": (ctypes.c_int, [vp, vp, ctypes.c_uint64, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -256,6 +274,17 @@ class Context:
         _check(lib().flb_kernel_times(self._h, _dptr(ms), n))
         return ms, np.array(list(n))
 
+    # -- device state and adjoint (pointers are device addresses) -----------
+    def get_state_device(self, ptr: int):
+        _check(lib().flb_get_state_device(self._h, ctypes.c_void_p(ptr)))
+
+    def set_state_device(self, ptr: int):
+        _check(lib().flb_set_state_device(self._h, ctypes.c_void_p(ptr)))
+
+    def adjoint_step(self, g_n: int, step: int, lam_next: int, lam: int, grad: int):
+        _check(lib().flb_adjoint_step(self._h, ctypes.c_void_p(g_n), int(step), ctypes.c_void_p(lam_next),
+                                      ctypes.c_void_p(lam), ctypes.c_void_p(grad)))
+
     # -- checkpoints ---------------------------------------------------------
     def save(self, path: str):
         _check(lib().flb_save(self._h, os.fsencode(path)))
@@ -268,5 +297,82 @@ class Context:
         return cls(0, (1, 1, 1), 1.0, _handle=h)
 
 
-__all__ = ["Context", "FLBError", "lib", "options", "EXPORTS", "D2Q9", "D3Q19", "FP64", "FP32", "BF16",
+class Batch:
+    """Independent D3Q19 ideal-gas replicas of uneven sizes (``flb_batch_*``)."""
+
+    def __init__(self, dims, omega_shear, kT, seeds, omega_bulk=None, omega_ghost=None, **opts):
+        L = lib()
+        n = len(dims)
+        d = np.ascontiguousarray(np.asarray(dims, dtype=np.int32).reshape(n, 3))
+        f = lambda v: None if v is None else _dptr(_f64(v, n, "per-replica value"))
+        self._keep = [np.ascontiguousarray(np.asarray(v, dtype=np.float64)) if v is not None else None
+                      for v in (omega_shear, omega_bulk, omega_ghost, kT)]
+        sd = (ctypes.c_uint64 * n)(*[int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds])
+        o = options(**opts)
+        h = ctypes.c_void_p()
+        oms, omb, omg, kts = self._keep
+        _check(L.flb_batch_create(ctypes.byref(h), D3Q19, n, d.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                  _dptr(oms), None if omb is None else _dptr(omb), None if omg is None else _dptr(omg),
+                                  _dptr(kts), sd, ctypes.byref(o)))
+        self._h = h
+        self.n = n
+        self.dims = [tuple(int(v) for v in row) for row in d]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().flb_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def init(self, thermal=False):
+        _check(lib().flb_batch_init(self._h, int(bool(thermal))))
+
+    def step(self, n=1):
+        _check(lib().flb_batch_step(self._h, int(n)))
+
+    def autotune(self):
+        sh = np.zeros((self.n, 3), dtype=np.int32)
+        _check(lib().flb_batch_autotune(self._h, sh.ctypes.data_as(ctypes.POINTER(ctypes.c_int))))
+        return sh
+
+    def mode_variance(self):
+        out = np.zeros((self.n, 19))
+        _check(lib().flb_batch_mode_variance(self._h, _dptr(out)))
+        return out
+
+    def structure_factor(self, replica, mode=0, accumulate=False):
+        X, Y, Z = self.dims[replica]
+        S = np.empty(X * Y * Z)
+        _check(lib().flb_batch_structure_factor(self._h, replica, _dptr(S), mode, int(bool(accumulate))))
+        return S
+
+    def get_populations(self, replica):
+        X, Y, Z = self.dims[replica]
+        f = np.empty((19, X * Y * Z))
+        _check(lib().flb_batch_get_populations(self._h, replica, _dptr(f)))
+        return f
+
+    def info(self):
+        n = ctypes.c_int()
+        s = ctypes.c_longlong()
+        st = ctypes.c_uint64()
+        _check(lib().flb_batch_info(self._h, ctypes.byref(n), ctypes.byref(s), ctypes.byref(st)))
+        return n.value, s.value, st.value
+
+    def synchronize(self):
+        _check(lib().flb_batch_synchronize(self._h))
+
+
+__all__ = ["Context", "Batch", "FLBError", "lib", "options", "EXPORTS", "D2Q9", "D3Q19", "FP64", "FP32", "BF16",
            "RHO", "U", "MODES", "MODE_VAR"]

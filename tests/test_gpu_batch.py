@@ -1,0 +1,83 @@
+"""Batched replicas (flb_batch_*): many independent D3Q19 ideal-gas lattices of
+uneven sizes in one persistent launch per step, replayed from a CUDA graph.
+
+Each replica must evolve exactly like a single lattice with the same
+parameters, Philox key and replica word: checked against the FP64 oracle and
+against a single-lattice context."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1012_3632_gb300 import Batch, Context
+
+pytestmark = pytest.mark.gpu
+
+# even X: two-site packed path; odd X: one-site path
+DIMS = [(8, 8, 8), (12, 10, 9), (6, 5, 4), (32, 16, 8), (7, 6, 5)]
+OMS = [1.2, 0.9, 1.55, 1.0, 1.3]
+KTS = [1e-5, 2e-5, 1e-4, 1e-5, 3e-5]
+SEEDS = [11, 2 ** 33 + 5, 7, 99, 3]
+OMB = [1.0, 1.1, 0.8, 1.0, 1.2]
+OMG = [1.0, 1.3, 1.2, 0.7, 1.5]
+
+
+def test_batch_replicas_match_oracle_and_single_lattice():
+    steps = 30
+    with Batch(DIMS, OMS, KTS, SEEDS, omega_bulk=OMB, omega_ghost=OMG) as b:
+        b.init(thermal=True)
+        b.step(steps)
+        for r, dims in enumerate(DIMS):
+            got = b.get_populations(r)
+            kw = dict(omega_shear=OMS[r], omega_bulk=OMB[r], omega_ghost=OMG[r], kT=KTS[r], seed=SEEDS[r])
+            p = oracle.Params(Q=19, dims=dims, replica=r, **kw)
+            want = oracle.run(p, oracle.init(p, thermal=True), 0, steps)
+            assert np.abs(got - want).max() <= 2e-5, r
+            with Context(19, dims, precision="fp32", replica=r, **kw) as c:
+                c.init(thermal=True)
+                c.step(steps)
+                assert np.abs(got - c.get_populations()).max() <= 1e-6, r
+
+
+def test_graph_replays_equal_single_steps():
+    with Batch(DIMS, OMS, KTS, SEEDS) as a, Batch(DIMS, OMS, KTS, SEEDS) as b:
+        a.init(thermal=True)
+        b.init(thermal=True)
+        a.step(7)  # three graph replays and one direct launch
+        for _ in range(7):
+            b.step(1)
+        a.step(4)
+        b.step(3)
+        b.step(1)
+        for r in range(len(DIMS)):
+            assert np.array_equal(a.get_populations(r), b.get_populations(r))
+        assert a.info()[2] == b.info()[2] == 11
+
+
+def test_autotune_keeps_state():
+    with Batch(DIMS, OMS, KTS, SEEDS) as b:
+        b.init(thermal=True)
+        b.step(3)
+        before = [b.get_populations(r) for r in range(len(DIMS))]
+        shapes = b.autotune()
+        assert shapes.shape == (len(DIMS), 3) and np.all(np.prod(shapes, axis=1) == 256)
+        for r in range(len(DIMS)):
+            assert np.array_equal(before[r], b.get_populations(r))
+        assert b.info()[2] == 3
+
+
+def test_ensemble_mode_temperatures():
+    """Every replica's modes equilibrate at its own kT (ensemble of 8 replicas)."""
+    dims = [(32, 32, 32), (24, 24, 24)] * 4
+    kts = [1e-5, 2e-5] * 4
+    oms = list(np.linspace(0.8, 1.6, 8))
+    N = np.array([1, 1 / 3, 1 / 3, 1 / 3, 2 / 3, 4 / 3, 4 / 9, 1 / 9, 1 / 9, 1 / 9, 2 / 27, 2 / 27, 2 / 27,
+                  2 / 9, 2 / 9, 2 / 9, 2 / 9, 1 / 3, 1 / 9])
+    with Batch(dims, oms, kts, list(range(100, 108))) as b:
+        b.init(thermal=True)
+        for _ in range(40):
+            b.step(25)
+            var = b.mode_variance()
+    T = (var / N / 3.0) / np.array(kts)[:, None]
+    V = np.array([np.prod(d) for d in dims])
+    T[:, :4] *= (V / (V - 1.0))[:, None]  # the site mean removes k = 0 of the conserved modes
+    assert np.all(np.abs(T.mean(axis=0) - 1) < 0.02), T.mean(axis=0)

@@ -76,18 +76,20 @@ def test_fp64_random_state_noise_rho0():
     assert np.abs(got - want).max() <= TOL["fp64"]
 
 
-def test_fp32_config1_like_100_steps():
-    """D3Q19 ideal, FP32 deviations, kT = 1e-5, rates (1.2, 1, 1), shear wave + thermal start."""
-    dims = (16, 16, 16)
+@pytest.mark.parametrize("dims", [(16, 16, 16), (17, 9, 8), (2, 5, 3)])
+def test_fp32_config1_like_100_steps(dims):
+    """D3Q19 ideal, FP32 deviations, kT = 1e-5, rates (1.2, 1, 1), shear wave + thermal start.
+    Even X runs the packed two-site kernel, odd X the one-site kernel."""
     u = inputs.shear_wave(dims, amp=1e-3)
     got, want = _run_both(19, dims, "fp32", 100, u=u, thermal=True, kT=1e-5, omega_shear=1.2, omega_bulk=1.0,
                           omega_ghost=1.0, seed=2)
     assert np.abs(got - want).max() <= TOL["fp32"]
 
 
-def test_fp32_config2_like_100_steps():
-    """D3Q19 non-ideal (A=-0.01, B=0.1, rho_c=1, kappa=0.02), FP32, kT = 1e-6, rates 1."""
-    dims = (16, 14, 12)
+@pytest.mark.parametrize("dims", [(16, 14, 12), (15, 12, 10), (2, 3, 4), (34, 6, 5)])
+def test_fp32_config2_like_100_steps(dims):
+    """D3Q19 non-ideal (A=-0.01, B=0.1, rho_c=1, kappa=0.02), FP32, kT = 1e-6, rates 1.
+    Even X runs the packed two-site kernel, odd X the one-site kernel."""
     rho = inputs.uniform_density(dims, seed=3)
     got, want = _run_both(19, dims, "fp32", 100, fe=FE, rho=rho, kT=1e-6, omega_shear=1.0, omega_bulk=1.0,
                           omega_ghost=1.0, seed=3)
