@@ -77,6 +77,14 @@ def step_bytes(wl):
 KERNEL_SOURCES = ("flb_device.cuh", "flb_kernels.cuh", "flb_prec.cuh")
 
 
+def kernel_name(wl):
+    """The step kernel the library launches for this workload."""
+    packed = wl["precision"] == "fp32" and wl["dims"][0] % 2 == 0 and wl["lattice"] == 19
+    if wl["fe"] and wl["lattice"] == 19:
+        return "k_step_march2" if packed else "k_step_march"
+    return "k_step2" if packed else "k_step"
+
+
 def kernel_source_hash():
     """Hash of the sources the step kernels are compiled from (ncu counters taken
     on other sources are stale)."""
@@ -435,7 +443,7 @@ def main():
         "data": "synthetic", "config": config_of(args, wl),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_kind": f"{peak_kind} copy bandwidth",
-                     "kernel": "k_step_march" if (wl["fe"] and wl["lattice"] == 19) else "k_step",
+                     "kernel": kernel_name(wl),
                      "what": "fused pull + moment-space MRT collide + Guo force + Philox/Box-Muller noise + store",
                      "bytes_per_site": fused_b, "sites_per_launch": V,
                      "avg_launch_ms": t_fused * 1e3},

@@ -442,18 +442,25 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 // of its column pair, and every stage (density gather, mu, F, collision) works
 // on site pairs with FADD2/FMUL2/FFMA2.  X must be even.  Same algorithm and
 // ring layout as k_step_march; the density and mu planes are stored as float2
-// pairs.
+// pairs.  GX = 4 (X % 4 == 0): the density gather works on quads of sites, one
+// 16-byte load per direction plus one 4-byte load for c_x = +-1, and the
+// density plane starts at x = xb - 4 so that its quads stay aligned; GX = 2:
+// it works on pairs and starts at xb - 2.
 // ---------------------------------------------------------------------------
-template <int TXT, int TY, int NZ, int MINB, bool GATHER = true>
+template <int TXT, int TY, int NZ, int MINB, int GX>
 __global__ void __launch_bounds__(TXT* TY, MINB)
-    k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<float> P, const float* __restrict__ drho)
+    k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<float> P)
 {
     using L = D3Q19;
+    constexpr bool QUAD = GX == 4;
     constexpr int NT = TXT * TY;
-    constexpr int RXP = TXT + 2, RY = TY + 4, RPP = RXP * RY;  // density pairs per plane (tile + 2 halo)
+    constexpr int OX = QUAD ? 4 : 2;                           // density plane starts at x = xb - OX
+    constexpr int RY = TY + 4;                                 // density rows (tile + 2 halo)
+    constexpr int RX = 2 * TXT + 2 * OX;                       // density floats per row
+    constexpr int RXG = RX / GX, RPG = RXG * RY;               // gather items (pairs or quads) per plane
     constexpr int MXP = TXT + 1, MY = TY + 2, MPP = MXP * MY;  // mu pairs per plane (tile + 1 halo)
-    constexpr int RX = 2 * RXP, MX = 2 * MXP;                  // floats per row
-    __shared__ __align__(16) float srho[5][RPP * 2];
+    constexpr int MX = 2 * MXP;                                // mu floats per row
+    __shared__ __align__(16) float srho[5][RX * RY];
     __shared__ __align__(16) float smu[3][MPP * 2];
     const int tid = threadIdx.x + TXT * threadIdx.y;
     const int X = a.X, Y = a.Y, Z = a.Z;
@@ -462,17 +469,19 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
     const int nz = min(NZ, Z - zb);
     const bool small = X < RX || Y < RY;
 
-    // density pairs of this thread: first site x (even), x-1, x+2 and rows
-    constexpr int NRH = (RPP + NT - 1) / NT;
+    // gather items of this thread (first site gx, a multiple of GX): the sites
+    // gx - 1, gx and gx + GX after periodic wrap, and the rows gy - 1, gy, gy + 1
+    constexpr int NRH = (RPG + NT - 1) / NT;
     int hx[NRH][3], hy[NRH][3];
 #pragma unroll
     for (int h = 0; h < NRH; ++h) {
-        const int e = min(tid + h * NT, RPP - 1);
-        const int gx = small ? wrap_any(xb - 2 + 2 * (e % RXP), X) : wrap_once(xb - 2 + 2 * (e % RXP), X);
-        const int gy = small ? wrap_any(yb - 2 + e / RXP, Y) : wrap_once(yb - 2 + e / RXP, Y);
+        const int e = min(tid + h * NT, RPG - 1);
+        const int gx0 = xb - OX + GX * (e % RXG), gy0 = yb - 2 + e / RXG;
+        const int gx = small ? wrap_any(gx0, X) : wrap_once(gx0, X);
+        const int gy = small ? wrap_any(gy0, Y) : wrap_once(gy0, Y);
         hx[h][0] = gx == 0 ? X - 1 : gx - 1;
         hx[h][1] = gx;
-        hx[h][2] = gx + 2 == X ? 0 : gx + 2;
+        hx[h][2] = gx + GX == X ? 0 : gx + GX;
         hy[h][0] = X * wrap_once(gy - 1, Y);
         hy[h][1] = X * gy;
         hy[h][2] = X * wrap_once(gy + 1, Y);
@@ -482,32 +491,51 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
 #pragma unroll
     for (int j = 0; j < NMU; ++j) {
         const int e = min(tid + j * NT, MPP - 1);
-        mc[j] = 2 * (e % MXP) + 1 + RX * (e / MXP + 1);
+        mc[j] = 2 * (e % MXP) + OX - 1 + RX * (e / MXP + 1);
     }
 
     const int x = xb + 2 * threadIdx.x, y = yb + threadIdx.y;
-    const int cm = 2 * threadIdx.x + 1 + MX * (threadIdx.y + 1);  // first site in the mu plane
-    const int cr = 2 * threadIdx.x + 2 + RX * (threadIdx.y + 2);  // first site in the density plane
+    const int cm = 2 * threadIdx.x + 1 + MX * (threadIdx.y + 1);   // first site in the mu plane
+    const int cr = 2 * threadIdx.x + OX + RX * (threadIdx.y + 2);  // first site in the density plane
     int ra = 3, mb = 2;
     int zc = wrap_any(zb - 2, Z);
-    // pair at float offset o of a plane: aligned 8-byte read when o is even
-    auto pair_at = [](const float* pl, int o, int cx) -> F2 {
-        if (cx == 0) return mk2(*reinterpret_cast<const float2*>(pl + o));
-        return F2(pl[o], pl[o + 1]);
-    };
 #pragma unroll 1
     for (int k = -4; k < nz; ++k) {
         const int ra1 = ra == 4 ? 0 : ra + 1, ra2 = ra1 == 4 ? 0 : ra1 + 1;
         const int mb1 = mb == 2 ? 0 : mb + 1, mb2 = mb1 == 2 ? 0 : mb1 + 1;
-        // (1) density pairs of plane zb+k+2, tile + 2 halo
+        // (1) density of plane zb+k+2, tile + 2 halo
         {
             const int zo[3] = {XY * (zc == 0 ? Z - 1 : zc - 1), XY * zc, XY * (zc == Z - 1 ? 0 : zc + 1)};
             float* out = srho[ra2];
 #pragma unroll
             for (int h = 0; h < NRH; ++h) {
                 const int e = tid + h * NT;
-                if (e < RPP) {
-                    if constexpr (GATHER) {
+                if (e < RPG) {
+                    if constexpr (QUAD) {
+                        // sites gx .. gx+3: pulls from gx-1 .. gx+4
+                        F2 glo[L::Q], ghi[L::Q], m[L::Q];
+#pragma unroll
+                        for (int i = 0; i < L::Q; ++i) {
+                            const float* p = P.src[i] + hy[h][1 - Vel<L>::cy(i)] + zo[1 - Vel<L>::cz(i)];
+                            const float4 v = *reinterpret_cast<const float4*>(p + hx[h][1]);
+                            const int cx = Vel<L>::cx(i);
+                            if (cx == 0) {
+                                glo[i] = F2(v.x, v.y);
+                                ghi[i] = F2(v.z, v.w);
+                            } else if (cx > 0) {
+                                glo[i] = F2(p[hx[h][0]], v.x);
+                                ghi[i] = F2(v.y, v.z);
+                            } else {
+                                glo[i] = F2(v.y, v.z);
+                                ghi[i] = F2(v.w, p[hx[h][2]]);
+                            }
+                        }
+                        L::moments(glo, m);
+                        const float2 lo = m[0].v;
+                        L::moments(ghi, m);
+                        *reinterpret_cast<float4*>(out + 4 * e) = make_float4(lo.x, lo.y, m[0].v.x, m[0].v.y);
+                    } else {
+                        // sites gx, gx+1: pulls from gx-1 .. gx+2
                         F2 g[L::Q], m[L::Q];
 #pragma unroll
                         for (int i = 0; i < L::Q; ++i) {
@@ -522,10 +550,6 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                         }
                         L::moments(g, m);
                         *reinterpret_cast<float2*>(out + 2 * e) = m[0].v;
-                    } else {
-                        // density written by the gather kernel of this step
-                        *reinterpret_cast<float2*>(out + 2 * e) =
-                            *reinterpret_cast<const float2*>(drho + hx[h][1] + hy[h][1] + zo[1]);
                     }
                 }
             }

@@ -23,13 +23,10 @@
 #define FLB_PACKED 1
 #endif
 #ifndef FLB_MARCH2_MINB
-#define FLB_MARCH2_MINB 4
+#define FLB_MARCH2_MINB 3
 #endif
 #ifndef FLB_MARCH2_TY
 #define FLB_MARCH2_TY 8
-#endif
-#ifndef FLB_NI_SPLIT
-#define FLB_NI_SPLIT 0
 #endif
 
 namespace flb {
@@ -414,12 +411,13 @@ struct Prec {
                         const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                         const dim3 b(TXT, TY, 1);
                         const dim3 g((m.X + 2 * TXT - 1) / (2 * TXT), (m.Y + TY - 1) / TY, (m.Z + NZ - 1) / NZ);
-                        if (FLB_NI_SPLIT)
-                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, false>
-                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V), (const float*)drho);
+                        // density gather by 16-byte quads when rows are 16-byte aligned
+                        if (m.X % 4 == 0)
+                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, 4>
+                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                         else
-                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, true>
-                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V), nullptr);
+                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, 2>
+                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                         return cudaGetLastError();
                     }
                 }
@@ -518,12 +516,7 @@ struct Prec {
     static int needs_density(const HostModel& m)
     {
         if (!m.nonideal) return 0;
-        if (m.Q == 9) return 1;
-        // packed FP32 D3Q19 with the split gather: the step reads the density field
-        return (std::is_same<R, float>::value && std::is_same<S, float>::value && m.X % 2 == 0 && FLB_PACKED &&
-                FLB_NI_SPLIT)
-                   ? 1
-                   : 0;
+        return m.Q == 9 ? 1 : 0;
     }
     static int rows(const HostModel& m)
     {

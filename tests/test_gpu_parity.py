@@ -86,7 +86,7 @@ def test_fp32_config1_like_100_steps(dims):
     assert np.abs(got - want).max() <= TOL["fp32"]
 
 
-@pytest.mark.parametrize("dims", [(16, 14, 12), (15, 12, 10), (2, 3, 4), (34, 6, 5)])
+@pytest.mark.parametrize("dims", [(16, 14, 12), (15, 12, 10), (2, 3, 4), (34, 6, 5), (72, 10, 6), (4, 5, 3)])
 def test_fp32_config2_like_100_steps(dims):
     """D3Q19 non-ideal (A=-0.01, B=0.1, rho_c=1, kappa=0.02), FP32, kT = 1e-6, rates 1.
     Even X runs the packed two-site kernel, odd X the one-site kernel."""
