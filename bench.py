@@ -53,11 +53,13 @@ WORKLOADS = {
                      name="D3Q19 ideal gas, 128^3 periodic, FP32 deviations, kT=1e-5, "
                           "omega=(1.2, 1.0, 1.0), shear wave + thermal start"),
 }
-# Algorithmic bytes per site of the fused step kernel: 19 pulled + 19 stored
-# populations.  The D3Q19 non-ideal kernel gathers the density it needs itself
-# (the re-reads of neighbouring populations come from L2), so its minimum DRAM
-# traffic is the same; the D2Q9 non-ideal step reads a density field written by
-# a separate gather kernel (Q pulled populations + 1 density written).
+# Algorithmic bytes per site and step of the path: every population is pulled
+# (read) and stored once, and the non-ideal fluid also reads every population
+# once more for the density gather, writes the density and reads it back (Q e +
+# 2 e_rho).  The D3Q19 non-ideal kernel does all of this in one launch and takes
+# the gather's re-reads and the density from L2 and shared memory, so its DRAM
+# minimum is that of the ideal step (2 Q e); the D2Q9 non-ideal step reads a
+# density field written by a separate gather kernel.
 ELEM = {"fp32": 4, "fp64": 8, "bf16": 2}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -65,13 +67,16 @@ CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.a
 
 
 def step_bytes(wl):
+    """(algorithmic bytes per site of the step kernel, of the gather kernel,
+    DRAM minimum per site of the step kernel)."""
     e = ELEM[wl["precision"]]
     Q = wl["lattice"]
     rb = 8 if wl["precision"] == "fp64" else 4
-    separate_gather = bool(wl["fe"]) and Q == 9
-    fused = 2 * Q * e + (rb if separate_gather else 0)
-    gather = Q * e + rb if separate_gather else 0
-    return fused, gather
+    if not wl["fe"]:
+        return 2 * Q * e, 0, 2 * Q * e
+    if Q == 9:
+        return 2 * Q * e + rb, Q * e + rb, 2 * Q * e + rb
+    return 3 * Q * e + 2 * rb, 0, 2 * Q * e
 
 
 KERNEL_SOURCES = ("flb_device.cuh", "flb_kernels.cuh", "flb_prec.cuh")
@@ -429,7 +434,7 @@ def main():
             dist.destroy_process_group()
         return
 
-    fused_b, gather_b = step_bytes(wl)
+    fused_b, gather_b, fused_min = step_bytes(wl)
     peak, peak_kind = measured_peak()
     n_fused = int(kn[1])
     t_fused = kms[1] / max(n_fused, 1) * 1e-3
@@ -446,7 +451,9 @@ def main():
                      "kernel": kernel_name(wl),
                      "what": "fused pull + moment-space MRT collide + Guo force + Philox/Box-Muller noise + store",
                      "bytes_per_site": fused_b, "sites_per_launch": V,
-                     "avg_launch_ms": t_fused * 1e3},
+                     "avg_launch_ms": t_fused * 1e3,
+                     "dram_min_bytes_per_site": fused_min,
+                     "frac_of_dram_min": fused_min * V / t_fused / 1e9 / peak},
         "kernels": {"density_gather": {"launches": int(kn[0]), "avg_ms": kms[0] / max(kn[0], 1),
                                        "bytes_per_site": gather_b,
                                        "achieved_gbs": gather_b * V / (kms[0] / max(kn[0], 1) * 1e-3) / 1e9
