@@ -48,6 +48,12 @@ WORKLOADS = {
                      omega=(1.2, 1.0, 1.0), seed=2,
                      name="D3Q19 ideal gas, 256^3 periodic, FP32 deviations, kT=1e-5, "
                           "omega=(1.2, 1.0, 1.0), shear wave + thermal start"),
+    "capillary1024x400": dict(lattice=9, dims=(1024, 400, 1), precision="fp32",
+                              fe=dict(A=-0.025, B=0.4, rho_c=0.75, kappa=0.08, total=True), kT=1e-7,
+                              omega=(1.0, 1.0, 1.0), seed=11, stripe=200,
+                              name="D2Q9 liquid stripe 1024x400 (thickness 200) of the Landau double well "
+                                   "beta (rho-0.5)^2 (rho-1)^2, beta=0.1, kappa=0.08, as total bulk free energy "
+                                   "(F = -rho grad mu + cs^2 grad rho), kT=1e-7, tau=1, FP32 deviations"),
     "ideal128": dict(lattice=19, dims=(128, 128, 128), precision="fp32", fe=None, kT=1e-5,
                      omega=(1.2, 1.0, 1.0), seed=2,
                      name="D3Q19 ideal gas, 128^3 periodic, FP32 deviations, kT=1e-5, "
@@ -80,6 +86,29 @@ def step_bytes(wl):
 
 
 KERNEL_SOURCES = ("flb_device.cuh", "flb_kernels.cuh", "flb_prec.cuh")
+
+
+def sample_dims(wl):
+    """Lattice of the CPU oracle's bounded sample (about 2.6e5 sites)."""
+    return (512, 512, 1) if wl["lattice"] == 9 else (64, 64, 64)
+
+
+def initial_density(wl, dims):
+    """Seeded initial density of a non-ideal workload (None for the ideal gas)."""
+    from paper_1012_3632_gb300 import inputs
+
+    if not wl["fe"]:
+        return None
+    if wl.get("stripe"):
+        X, Y = dims[0], dims[1]
+        th = wl["stripe"] * Y / wl["dims"][1]
+        fe = wl["fe"]
+        D = (-fe["A"] / fe["B"]) ** 0.5  # half the liquid-vapour gap of the double well
+        rho_l, rho_v = fe["rho_c"] + D, fe["rho_c"] - D
+        beta = fe["B"] / 4
+        w = (8 * fe["kappa"] / beta) ** 0.5 / (rho_l - rho_v)
+        return inputs.stripe_density(X, Y, rho_l, rho_v, w, 0.5 * (Y - th), 0.5 * (Y + th)).ravel()
+    return inputs.uniform_density(dims, seed=wl["seed"])
 
 
 def kernel_name(wl):
@@ -174,12 +203,12 @@ def cpu_baseline(wl, budget_s=12.0):
     import oracle
     from paper_1012_3632_gb300 import inputs
 
-    dims = (64, 64, 64)
+    dims = sample_dims(wl)
     om = wl["omega"]
     fe = wl["fe"] or {}
     p = oracle.Params(Q=wl["lattice"], dims=dims, omega_shear=om[0], omega_bulk=om[1], omega_ghost=om[2],
                       kT=wl["kT"], nonideal=bool(wl["fe"]), seed=wl["seed"], **fe)
-    rho = inputs.uniform_density(dims, seed=wl["seed"]) if wl["fe"] else None
+    rho = initial_density(wl, dims)
     f = oracle.init(p, rho=rho, thermal=not wl["fe"])
     t0 = time.perf_counter()
     steps = 0
@@ -298,12 +327,12 @@ def run_reference(args, wl, rank):
     import oracle
     from paper_1012_3632_gb300 import inputs
 
-    dims = (64, 64, 64)
+    dims = sample_dims(wl)
     om = wl["omega"]
     fe = wl["fe"] or {}
     p = oracle.Params(Q=wl["lattice"], dims=dims, omega_shear=om[0], omega_bulk=om[1], omega_ghost=om[2],
                       kT=wl["kT"], nonideal=bool(wl["fe"]), seed=wl["seed"], **fe)
-    rho = inputs.uniform_density(dims, seed=wl["seed"]) if wl["fe"] else None
+    rho = initial_density(wl, dims)
     f = oracle.init(p, rho=rho, thermal=not wl["fe"])
     for t in range(args.warmup):
         f = oracle.step(p, f, t)
@@ -375,7 +404,7 @@ def main():
     V = dims[0] * dims[1] * dims[2]
     ctx = Context(wl["lattice"], dims, om[0], om[1], om[2], kT=wl["kT"], free_energy=wl["fe"], seed=wl["seed"],
                   precision=wl["precision"], replica=rank, stream=stream.cuda_stream, device=local)
-    rho = inputs.uniform_density(dims, seed=wl["seed"]) if wl["fe"] else None
+    rho = initial_density(wl, dims)
     u = None if wl["fe"] else inputs.shear_wave(dims, amp=1e-3)
     ctx.init(rho=rho, u=u, thermal=not wl["fe"])
 

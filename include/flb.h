@@ -94,11 +94,23 @@ typedef enum {
                          returns the mean over snapshots of (1/V) sum_r (m_a - <m_a>_r)^2 */
 } flb_observable;
 
-/* Square-gradient free energy of the non-ideal fluid (App. A, Eq. (freeE-funct)),
- * psi being the excess over the ideal lattice gas.  enabled = 0: ideal gas. */
+/* Square-gradient free energy of the non-ideal fluid (App. A, Eq. (freeE-funct)):
+ * psi(rho) = A (rho - rho_c)^2 / 2 + B (rho - rho_c)^4 / 4 and the gradient term
+ * kappa |grad rho|^2 / 2, mu = psi'(rho) - kappa lap rho.  The force is
+ *   total = 0: F = -rho grad mu; psi is the excess over the ideal lattice gas,
+ *              whose pressure rho cs^2 the LB supplies itself;
+ *   total = 1: F = -rho grad mu + cs^2 grad rho; psi is the total bulk free
+ *              energy f0 and F is Eq. (he-force), kappa rho grad lap rho -
+ *              grad(p0 - rho cs^2) with grad p0 = rho grad f0' (p0 = rho f0' - f0).
+ *              The Landau double well of Sec. VI, beta (rho - rho_V)^2 (rho - rho_L)^2,
+ *              is A = -beta (rho_L - rho_V)^2, B = 4 beta, rho_c = (rho_L + rho_V) / 2.
+ * Gradients and Laplacians are the isotropic lattice stencils
+ * grad phi = (1/cs^2) sum_i w_i c_i phi(r + c_i), lap phi = (2/cs^2) sum_i w_i (phi(r + c_i) - phi(r)).
+ * enabled = 0: ideal gas. */
 typedef struct {
     int enabled;
     double A, B, rho_c, kappa;
+    int total;
 } flb_free_energy;
 
 typedef struct {
@@ -159,11 +171,45 @@ int flb_moments(flb_ctx* ctx, double* out, int which);
 int flb_structure_factor(flb_ctx* ctx, double* S, int mode, int accumulate);
 
 /* Number of snapshots accumulated for structure factors of `mode`
- * (mode = -1: the FLB_MODE_VAR accumulators). */
+ * (mode = -1: the FLB_MODE_VAR accumulators; mode = -2: flb_height_spectrum). */
 int flb_snapshot_count(flb_ctx* ctx, int mode, int* count);
 
 /* Clear every snapshot accumulator. */
 int flb_reset_accumulators(flb_ctx* ctx);
+
+/* ---- Capillary fluctuations of a liquid stripe (Sec. VI) ------------------
+ * A 2-D (D2Q9) state holding a liquid stripe between two interfaces normal to
+ * y: the lower one (vapour below, liquid above) near row guess[0], the upper
+ * one (liquid below, vapour above) near row guess[1]. */
+typedef struct {
+    double rho_l, rho_v; /* liquid and vapour density of the fitted profile */
+    double width;        /* interface width w of Eq. (interf-width), > 0 */
+    double guess[2];     /* rows of the lower and the upper interface */
+    int window;          /* rows fitted on each side of round(guess[i]); >= 1, 2 window + 1 <= Y */
+    int iterations;      /* Gauss-Newton iterations from h = guess[i]; 1..100 */
+} flb_interface_fit;
+
+/* Heights of the two interfaces in every column (Eq. (height-def)): for each
+ * column x and interface i, h minimizes
+ *   sum over rows y = c - window .. c + window (c = round(guess[i]), periodic)
+ *   of (rho(x, y) - rho_MF(y - h))^2,
+ *   rho_MF(s) = (rho_l + rho_v)/2 +- (rho_l - rho_v)/2 tanh(2 s / width)
+ * (the mean-field profile of Eq. (denprof); + for the lower interface), by
+ * `iterations` Gauss-Newton steps from h = guess[i].  rho is the pre-collision
+ * density of the current state.  h: host, 2 X doubles (lower interface first,
+ * caller-owned).  FLB_EINVAL for a D3Q19 context or invalid fit parameters. */
+int flb_interface_heights(flb_ctx* ctx, const flb_interface_fit* fit, double* h);
+
+/* Height spectrum of the two interfaces, averaged over both:
+ *   S(k_n) = (1/2) sum_i |sum_x (h_i(x) - <h_i>) e^{-2 pi i n x / X}|^2 / X,
+ * n = 0 .. X-1 (S(0) = 0), the quantity Eq. (capill-static) compares with
+ * kT / (sigma (2 - 2 cos k)) on the lattice.  accumulate = 1 adds the current
+ * state to the running sum (count: flb_snapshot_count with mode -2) and S
+ * receives the mean over the snapshots; accumulate = 0 returns the current
+ * state's spectrum.  S: host, X doubles, or NULL.  Errors as
+ * flb_interface_heights; device memory (a few X doubles) is allocated on the
+ * first call. */
+int flb_height_spectrum(flb_ctx* ctx, const flb_interface_fit* fit, double* S, int accumulate);
 
 /* Total mass and momentum of the current state, summed on the GPU in double:
  * out[0] = sum rho, out[1..3] = sum_r sum_i f_i c_i (z component 0 for D2Q9). */

@@ -48,6 +48,7 @@ class _Params(ctypes.Structure):
         ("nonideal", ctypes.c_int),
         ("A", ctypes.c_double), ("B", ctypes.c_double), ("rho_c", ctypes.c_double),
         ("kappa", ctypes.c_double),
+        ("total", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("replica", ctypes.c_uint32),
     ]
@@ -72,6 +73,7 @@ class Params:
     B: float = 0.0
     rho_c: float = 1.0
     kappa: float = 0.0
+    total: bool = False
     seed: int = 1
     replica: int = 0
     origin: tuple = (0, 0, 0)
@@ -97,7 +99,7 @@ class Params:
         return _Params(self.Q, X, Y, Z, ox, oy, oz, wx, wy, wz,
                        self.omega_shear, self.omega_bulk, self.omega_ghost,
                        self.kT, self.rho0, int(self.noise_rho_local), int(self.nonideal),
-                       self.A, self.B, self.rho_c, self.kappa,
+                       self.A, self.B, self.rho_c, self.kappa, int(self.total),
                        self.seed & 0xFFFFFFFFFFFFFFFF, self.replica & 0xFFFFFFFF)
 
     def with_(self, **kw) -> "Params":

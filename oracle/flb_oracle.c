@@ -80,6 +80,7 @@ typedef struct {
     int noise_rho_local;
     int nonideal;
     double A, B, rho_c, kappa;   /* psi(rho) = A (rho-rho_c)^2/2 + B (rho-rho_c)^4/4 */
+    int total;                   /* psi is the total bulk free energy f0 of App. A */
     uint64_t seed;
     uint32_t replica;
 } orc_params;
@@ -433,7 +434,14 @@ static double psi_prime(const orc_params* p, double rho)
 }
 
 /* rho[V], F[3V] of the state f.  Sites whose stencil leaves the window get NaN.
- * For the ideal gas F = 0. */
+ * For the ideal gas F = 0.
+ *
+ * psi the excess free energy over the ideal lattice gas (default):
+ *   F = -rho grad mu.
+ * psi the total bulk free energy f0 (total = 1), Eq. (he-force) as printed:
+ *   F = kappa rho grad lap rho - grad(p0 - rho s2) with grad p0 = rho grad f0'
+ *     = -rho grad mu + s2 grad rho,
+ * the last term cancelling the ideal-gas pressure the LB carries itself. */
 static void density_force(const orc_params* p, const orc_lattice* L, const double* f, double* rho,
                           double* F)
 {
@@ -469,6 +477,15 @@ static void density_force(const orc_params* p, const orc_lattice* L, const doubl
                     for (int d = 0; d < 3; d++) g[d] += L->w[i] * L->c[i][d] * mun;
                 }
                 for (int d = 0; d < 3; d++) F[d * V + s] = -rho[s] * g[d] / S2;
+                if (p->total) {
+                    double gr[3] = {0, 0, 0};
+                    for (int i = 0; i < L->Q; i++) {
+                        long n = nbr(p, x, y, z, L->c[i][0], L->c[i][1], L->c[i][2]);
+                        double rn = (n < 0) ? NAN : rho[n];
+                        for (int d = 0; d < 3; d++) gr[d] += L->w[i] * L->c[i][d] * rn;
+                    }
+                    for (int d = 0; d < 3; d++) F[d * V + s] += S2 * (gr[d] / S2);
+                }
             }
     free(mu);
 }

@@ -75,7 +75,10 @@ class Ref:
         d = rho - self.p.rho_c
         mu = A * d + B * d ** 3 - kappa * lap
         grad = torch.stack([sum(w[i] * c[i, a] * self._at(mu, c[i]) for i in range(1, 19)) / CS2 for a in range(3)])
-        return -rho * grad
+        F = -rho * grad
+        if self.p.total:  # + cs^2 grad rho (ideal-gas pressure of the LB cancelled)
+            F = F + torch.stack([sum(w[i] * c[i, a] * self._at(rho, c[i]) for i in range(1, 19)) for a in range(3)])
+        return F
 
     def step(self, g, theta, z):
         """g: (19, Z, Y, X) pre-collision deviations -> next pre-collision deviations."""

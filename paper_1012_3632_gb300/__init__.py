@@ -5,4 +5,4 @@ The compute path is the CUDA library ``libflb.so`` (C ABI in
 the seeded synthetic input generators.
 """
 from .flb import (BF16, D2Q9, D3Q19, FP32, FP64, MODE_VAR, MODES, RHO, U, Batch, Context, FLBError,  # noqa: F401
-                  lib, options)
+                  interface_fit, landau_free_energy, landau_width, lib, options)

@@ -27,7 +27,7 @@ def _context(dims, theta, cfg):
     th = [float(v) for v in theta.detach().cpu().tolist()]
     fe = None
     if cfg.get("nonideal", True):
-        fe = dict(A=th[4], B=th[5], rho_c=cfg.get("rho_c", 1.0), kappa=th[3])
+        fe = dict(A=th[4], B=th[5], rho_c=cfg.get("rho_c", 1.0), kappa=th[3], total=cfg.get("total", False))
     return Context(D3Q19, dims, th[0], th[1], th[2], kT=cfg["kT"], free_energy=fe, seed=cfg["seed"],
                    precision=cfg["precision"], rho0=cfg.get("rho0", 1.0), replica=cfg.get("replica", 0),
                    noise_rho_local=cfg.get("noise_rho_local", True),

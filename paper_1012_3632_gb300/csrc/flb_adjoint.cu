@@ -52,7 +52,7 @@ struct AdjArgs {
     int X, Y, Z;
     long V;
     int nonideal;
-    R A, B, kappa, rho0_minus_rhoc;
+    R A, B, kappa, rho0_minus_rhoc, pgrad;
     // d(rel)/d omega = -1/N_a, d(frc)/d omega = -1/(2 N_a), d(ns)/d omega per mode
     R drel[16], dfrc[6], dns[16];
     int cls[16];  // 0 bulk, 1 shear, 2 ghost of non-conserved mode k
@@ -222,7 +222,10 @@ __global__ void k_adj_collide(const AdjArgs<R> a, uint32_t step, const R* __rest
     block_rows<3>(gp, rows + blin() * 6);
 }
 
-// mubar(y) = -3 sum_i w_i c_i . rho(y - c_i) Fbar(y - c_i);  rb1(y) = Fbar . F / rho
+// F(r) = -rho(r) grad mu(r) + pgrad sum_i w_i c_i rho(r + c_i).  Adjoint:
+// mubar(y) = -3 sum_i w_i c_i . rho(y - c_i) Fbar(y - c_i);
+// rb1(y) = Fbar(y) . (-grad mu(y)) + pgrad sum_i w_i c_i . Fbar(y - c_i),
+// with -grad mu(y) = (F(y) - pgrad sum_i w_i c_i rho(y + c_i)) / rho(y).
 template <class R>
 __global__ void k_adj_mu(const AdjArgs<R> a, const R* __restrict__ drho, const R* __restrict__ F,
                          const R* __restrict__ Fbar, R* __restrict__ mubar, R* __restrict__ rb1)
@@ -234,17 +237,24 @@ __global__ void k_adj_mu(const AdjArgs<R> a, const R* __restrict__ drho, const R
     const long V = a.V;
     const int s = x + a.X * (y + a.Y * z);
     const Nbhd nb(x, y, z, a.X, a.Y, a.Z);
-    R acc = R(0);
+    R acc = R(0), accp = R(0), pr[3] = {R(0), R(0), R(0)};
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         const int q = nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i));  // y - c_i
         const R rq = a.c.rho0 + drho[q];
         const R cf = Vel<L>::cx(i) * Fbar[q] + Vel<L>::cy(i) * Fbar[V + q] + Vel<L>::cz(i) * Fbar[2 * V + q];
         acc += R(Vel<L>::w(i)) * rq * cf;
+        accp += R(Vel<L>::w(i)) * cf;
+        const R wr = R(Vel<L>::w(i)) * drho[nb.src(-Vel<L>::cx(i), -Vel<L>::cy(i), -Vel<L>::cz(i))];  // y + c_i
+        pr[0] += R(Vel<L>::cx(i)) * wr;
+        pr[1] += R(Vel<L>::cy(i)) * wr;
+        pr[2] += R(Vel<L>::cz(i)) * wr;
     }
     mubar[s] = R(-3) * acc;
     const R rho = a.c.rho0 + drho[s];
-    rb1[s] = (Fbar[s] * F[s] + Fbar[V + s] * F[V + s] + Fbar[2 * V + s] * F[2 * V + s]) / rho;
+    R fg = R(0);
+    for (int d = 0; d < 3; ++d) fg += Fbar[d * V + s] * (F[d * V + s] - a.pgrad * pr[d]);
+    rb1[s] = fg / rho + a.pgrad * accp;
 }
 
 // rhobar = rb1 + psi''(rho) mubar - kappa lap(mubar), added to every population;
@@ -311,6 +321,7 @@ AdjArgs<R> make_adj(const HostModel& m, const Coll<R>& c)
     a.B = R(m.B);
     a.kappa = R(m.kappa);
     a.rho0_minus_rhoc = R(m.rho0 - m.rho_c);
+    a.pgrad = R(m.nonideal && m.total ? 1 : 0);
     for (int k = 0; k < 15; ++k) {
         const int aidx = 4 + k;
         const double om = k == 0 ? m.om_b : k < 6 ? m.om_s : m.om_g;
@@ -353,6 +364,7 @@ cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, 
         sa.B = a.B;
         sa.kappa = a.kappa;
         sa.rho0_minus_rhoc = a.rho0_minus_rhoc;
+        sa.pgrad = a.pgrad;
         k_mu<L, R><<<g, b, 0, st>>>(sa, drho, mu);
         k_force<L, R><<<g, b, 0, st>>>(sa, drho, mu, F);
     }

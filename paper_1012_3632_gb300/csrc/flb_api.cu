@@ -84,6 +84,14 @@ struct flb_ctx {
     std::vector<double> mv_sum;         // per-mode sum over snapshots of the site variance
     int mv_count = 0;
 
+    // interface heights and height spectrum of a stripe
+    double* h_dev = nullptr;            // 2 X heights
+    double2* hs_work = nullptr;         // 2 X complex
+    double2* hs_scratch = nullptr;
+    double* hs_acc = nullptr;           // X
+    double* hs_tmp = nullptr;
+    int hs_count = 0;
+
     // adjoint scratch
     void* adj_work = nullptr;
     double* adj_rows = nullptr;
@@ -118,7 +126,8 @@ int alloc(void** p, size_t bytes)
 void free_all(flb_ctx* c)
 {
     void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
-                    c->adj_work, c->adj_rows, c->adj_col};
+                    c->adj_work, c->adj_rows, c->adj_col, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
+                    c->hs_tmp};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (double* p : c->sk_acc)
@@ -299,6 +308,7 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
         m.B = fe->B;
         m.rho_c = fe->rho_c;
         m.kappa = fe->kappa;
+        m.total = fe->total ? 1 : 0;
     } else {
         m.nonideal = 0;
         m.rho_c = o.rho0;
@@ -477,6 +487,10 @@ int flb_snapshot_count(flb_ctx* c, int mode, int* count)
         *count = c->mv_count;
         return FLB_OK;
     }
+    if (mode == -2) {
+        *count = c->hs_count;
+        return FLB_OK;
+    }
     if (mode < 0 || mode >= c->m.Q) return fail(FLB_EINVAL, "mode out of range");
     *count = c->sk_count[mode];
     return FLB_OK;
@@ -488,6 +502,76 @@ int flb_reset_accumulators(flb_ctx* c)
     for (auto& n : c->sk_count) n = 0;
     for (auto& v : c->mv_sum) v = 0.0;
     c->mv_count = 0;
+    c->hs_count = 0;
+    return FLB_OK;
+}
+
+namespace {
+
+int check_fit(const flb_ctx* c, const flb_interface_fit* f)
+{
+    if (!f) return fail(FLB_EINVAL, "fit is NULL");
+    if (c->m.Q != 9) return fail(FLB_EINVAL, "interface heights need a D2Q9 context");
+    if (!(f->width > 0) || !std::isfinite(f->rho_l) || !std::isfinite(f->rho_v) || f->rho_l == f->rho_v)
+        return fail(FLB_EINVAL, "fit: width must be > 0 and rho_l != rho_v");
+    if (f->window < 1 || 2 * f->window + 1 > c->m.Y) return fail(FLB_EINVAL, "fit: window must be in [1, (Y-1)/2]");
+    if (f->iterations < 1 || f->iterations > 100) return fail(FLB_EINVAL, "fit: iterations must be in [1, 100]");
+    for (int i = 0; i < 2; ++i)
+        if (!std::isfinite(f->guess[i]) || std::fabs(f->guess[i]) > 1e9) return fail(FLB_EINVAL, "fit: bad guess");
+    return FLB_OK;
+}
+
+// Heights of the current state into c->h_dev.
+int heights_device(flb_ctx* c, const flb_interface_fit* f)
+{
+    const HostModel& m = c->m;
+    int rc;
+    if ((rc = alloc((void**)&c->h_dev, 2 * (size_t)m.X * sizeof(double)))) return rc;
+    FLB_CUDA(c->ops->density(m, c->buf[c->cur], c->drho, c->stream));
+    FLB_CUDA(flb::interface_heights(c->drho, c->ops->real_size, m.rho0, m.X, m.Y, *f, c->h_dev, c->stream));
+    return FLB_OK;
+}
+
+}  // namespace
+
+int flb_interface_heights(flb_ctx* c, const flb_interface_fit* fit, double* h)
+{
+    if (!c || !h) return fail(FLB_EINVAL, "ctx or h is NULL");
+    int rc;
+    if ((rc = check_fit(c, fit))) return rc;
+    DeviceGuard guard(c->device);
+    if ((rc = heights_device(c, fit))) return rc;
+    FLB_CUDA(cudaMemcpyAsync(h, c->h_dev, 2 * (size_t)c->m.X * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    FLB_CUDA(cudaStreamSynchronize(c->stream));
+    return FLB_OK;
+}
+
+int flb_height_spectrum(flb_ctx* c, const flb_interface_fit* fit, double* S, int accumulate)
+{
+    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
+    int rc;
+    if ((rc = check_fit(c, fit))) return rc;
+    DeviceGuard guard(c->device);
+    const int X = c->m.X;
+    if ((rc = alloc((void**)&c->hs_work, 2 * (size_t)X * sizeof(double2))) ||
+        (rc = alloc((void**)&c->hs_scratch, 2 * (size_t)X * sizeof(double2))) ||
+        (rc = alloc((void**)&c->hs_acc, (size_t)X * sizeof(double))) ||
+        (rc = alloc((void**)&c->hs_tmp, (size_t)X * sizeof(double))))
+        return rc;
+    if ((rc = heights_device(c, fit))) return rc;
+    if (accumulate && c->hs_count == 0) FLB_CUDA(cudaMemsetAsync(c->hs_acc, 0, X * sizeof(double), c->stream));
+    FLB_CUDA(flb::height_power(c->h_dev, X, c->hs_work, c->hs_scratch, accumulate ? c->hs_acc : nullptr, c->hs_tmp,
+                               c->stream));
+    if (accumulate) c->hs_count += 1;
+    if (S) {
+        FLB_CUDA(cudaMemcpyAsync(S, accumulate ? c->hs_acc : c->hs_tmp, X * sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
+        FLB_CUDA(cudaStreamSynchronize(c->stream));
+        if (accumulate) {
+            const double inv = 1.0 / c->hs_count;
+            for (int k = 0; k < X; ++k) S[k] *= inv;
+        }
+    }
     return FLB_OK;
 }
 

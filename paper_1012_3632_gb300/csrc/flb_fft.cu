@@ -236,6 +236,11 @@ static cudaError_t fft_axis(double2* data, double2* scratch, int L, long es, lon
     return cudaMemcpyAsync(data, scratch, V * sizeof(double2), cudaMemcpyDeviceToDevice, s);
 }
 
+cudaError_t fft_rows(double2* data, int X, int n, double2* scratch, cudaStream_t s)
+{
+    return fft_axis(data, scratch, X, 1, X, n, (long)X * n, 1, (long)X * n, s);
+}
+
 cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s)
 {
     const long V = (long)X * Y * Z;

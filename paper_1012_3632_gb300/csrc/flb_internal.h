@@ -8,6 +8,8 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/flb.h"
+
 namespace flb {
 
 // Model parameters in double; each instantiation converts to its compute type.
@@ -18,6 +20,7 @@ struct HostModel {
     double om_s, om_b, om_g, kT;
     int nonideal;
     double A, B, rho_c, kappa;
+    int total;  // psi is the total bulk free energy: mu carries -cs^2 ln rho
     uint64_t seed;
     uint32_t replica;
     int noise_local;
@@ -69,6 +72,17 @@ int set_error(int code, const std::string& msg);
 
 // In-place forward DFT along every axis of length > 1 of a complex X*Y*Z field.
 cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s);
+// In-place forward DFT of n consecutive rows of length X (scratch: X n elements).
+cudaError_t fft_rows(double2* data, int X, int n, double2* scratch, cudaStream_t s);
+
+// Interface heights of a stripe (flb_capillary.cu): drho is the density
+// deviation field (real_size 4 or 8 bytes), h receives 2 X doubles.
+cudaError_t interface_heights(const void* drho, int real_size, double rho0, int X, int Y,
+                              const flb_interface_fit& f, double* h, cudaStream_t s);
+// Height spectrum of the 2 X heights h: work and scratch hold 2 X complex
+// doubles; accumulate: acc += p, else out = p (X doubles).
+cudaError_t height_power(const double* h, int X, double2* work, double2* scratch, double* acc, double* out,
+                         cudaStream_t s);
 
 // Adjoint of one D3Q19 step (flb_adjoint.cu): gn, lam_next, lam are [19][V]
 // pre-collision deviations / adjoints in the storage type (FP64 or FP32);

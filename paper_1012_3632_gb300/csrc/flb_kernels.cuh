@@ -126,8 +126,11 @@ struct StepArgs {
     int X, Y, Z;
     long V;
     // non-ideal fluid: psi'(rho) = A (rho - rho_c) + B (rho - rho_c)^3, with
-    // rho - rho_c = drho + rho0_minus_rhoc
-    R A, B, kappa, rho0_minus_rhoc;
+    // rho - rho_c = drho + rho0_minus_rhoc; mu = psi' - kappa lap rho.
+    // pgrad = 1 when psi is the total bulk free energy: F = -rho grad mu gains
+    // cs^2 grad rho = sum_i w_i c_i rho(r + c_i), which cancels the LB's own
+    // ideal-gas pressure gradient (Eq. (he-force)); pgrad = 0 otherwise.
+    R A, B, kappa, rho0_minus_rhoc, pgrad;
 };
 
 // ---------------------------------------------------------------------------
@@ -206,11 +209,21 @@ __global__ void __launch_bounds__(TX* TY* TZ)
             if (Vel<L>::cy(i)) gy += R(Vel<L>::cy(i)) * wm;
             if (Vel<L>::cz(i)) gz += R(Vel<L>::cz(i)) * wm;
         }
-        const R rho = a.c.rho0 + srho[(threadIdx.x + 2) + RX * ((threadIdx.y + 2) + RY * (threadIdx.z + HZ))];
+        const int cr = (threadIdx.x + 2) + RX * ((threadIdx.y + 2) + RY * (threadIdx.z + HZ));
+        const R rho = a.c.rho0 + srho[cr];
         const R pre = R(-3) * rho;
         F[0] = pre * gx;
         F[1] = pre * gy;
         F[2] = pre * gz;
+        if (a.pgrad != R(0)) {
+#pragma unroll
+            for (int i = 1; i < L::Q; ++i) {
+                const R wr = R(Vel<L>::w(i)) * srho[cr + Vel<L>::cx(i) + RX * (Vel<L>::cy(i) + RY * Vel<L>::cz(i))];
+                if (Vel<L>::cx(i)) F[0] += R(Vel<L>::cx(i)) * wr;
+                if (Vel<L>::cy(i)) F[1] += R(Vel<L>::cy(i)) * wr;
+                if (Vel<L>::cz(i)) F[2] += R(Vel<L>::cz(i)) * wr;
+            }
+        }
     }
     if (x >= X || y >= Y || z >= Z) return;
     const Nbhd nb(x, y, z, X, Y, Z);
@@ -422,11 +435,27 @@ __global__ void __launch_bounds__(TX* TY, MINB)
                 if (Vel<L>::cz(i)) gz += R(Vel<L>::cz(i)) * wm;
             }
             const R pre = R(-3) * (a.c.rho0 + srho[ra][cr]);
+            R fx = pre * gx, fy = pre * gy, fz = pre * gz;
+            if (a.pgrad != R(0)) {
+                // + cs^2 grad rho from the density planes z-1, z, z+1
+                const R* qlo = srho[ra == 0 ? 4 : ra - 1];
+                const R* qmid = srho[ra];
+                const R* qhi = srho[ra1];
+#pragma unroll
+                for (int i = 1; i < L::Q; ++i) {
+                    const int cz = Vel<L>::cz(i);
+                    const R* pl = cz > 0 ? qhi : (cz < 0 ? qlo : qmid);
+                    const R wr = R(Vel<L>::w(i)) * pl[cr + Vel<L>::cx(i) + RX * Vel<L>::cy(i)];
+                    if (Vel<L>::cx(i)) fx += R(Vel<L>::cx(i)) * wr;
+                    if (Vel<L>::cy(i)) fy += R(Vel<L>::cy(i)) * wr;
+                    if (Vel<L>::cz(i)) fz += R(Vel<L>::cz(i)) * wr;
+                }
+            }
             const Nbhd nb(x, y, z, X, Y, Z);
             R g[L::Q];
             pull_planes<L, true>(P, nb, g);
             const int s = x + X * (y + Y * z);
-            L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
+            L::collide(g, fx, fy, fz, a.c, (uint32_t)s, a.c.step);
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) store_stream(P.dst[i] + s, g[i]);
         }
@@ -445,7 +474,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 // pairs.  GX = 4 (X % 4 == 0): the density gather works on quads of sites, one
 // 16-byte load per direction plus one 4-byte load for c_x = +-1, and the
 // density plane starts at x = xb - 4 so that its quads stay aligned; GX = 2:
-// it works on pairs and starts at xb - 2.
+// it works on pairs and starts at xb - 2.  Excess free energy only
+// (pgrad = 0): the total-free-energy force runs through k_step_march.
 // ---------------------------------------------------------------------------
 template <int TXT, int TY, int NZ, int MINB, int GX>
 __global__ void __launch_bounds__(TXT* TY, MINB)

@@ -74,6 +74,7 @@ StepArgs<R> make_args(const HostModel& m, uint64_t step)
     a.B = R(m.B);
     a.kappa = R(m.kappa);
     a.rho0_minus_rhoc = R(m.rho0 - m.rho_c);
+    a.pgrad = R(m.nonideal && m.total ? 1 : 0);
     return a;
 }
 
@@ -257,16 +258,20 @@ __global__ void k_force(const StepArgs<R> a, const R* __restrict__ drho, const R
     if (x >= a.X || y >= a.Y || z >= a.Z) return;
     const int s = x + a.X * (y + a.Y * z);
     const Nbhd nb(x, y, z, a.X, a.Y, a.Z);
-    R gr[3] = {R(0), R(0), R(0)};
+    R gr[3] = {R(0), R(0), R(0)}, pr[3] = {R(0), R(0), R(0)};
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
-        const R wm = R(Vel<L>::w(i)) * mu[nb.src(-Vel<L>::cx(i), -Vel<L>::cy(i), -Vel<L>::cz(i))];
+        const int q = nb.src(-Vel<L>::cx(i), -Vel<L>::cy(i), -Vel<L>::cz(i));  // r + c_i
+        const R wm = R(Vel<L>::w(i)) * mu[q], wr = R(Vel<L>::w(i)) * drho[q];
         gr[0] += R(Vel<L>::cx(i)) * wm;
         gr[1] += R(Vel<L>::cy(i)) * wm;
         gr[2] += R(Vel<L>::cz(i)) * wm;
+        pr[0] += R(Vel<L>::cx(i)) * wr;
+        pr[1] += R(Vel<L>::cy(i)) * wr;
+        pr[2] += R(Vel<L>::cz(i)) * wr;
     }
     const R pre = R(-3) * (a.c.rho0 + drho[s]);
-    for (int d = 0; d < 3; ++d) F[d * a.V + s] = pre * gr[d];
+    for (int d = 0; d < 3; ++d) F[d * a.V + s] = pre * gr[d] + a.pgrad * pr[d];
 }
 
 // Block sum of NV doubles per thread into out[0..NV) (one row per block).
@@ -406,7 +411,7 @@ struct Prec {
         if (m.Q == 19) {
             if (m.nonideal) {
                 if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
-                    if (m.X % 2 == 0 && FLB_PACKED) {
+                    if (m.X % 2 == 0 && FLB_PACKED && !m.total) {
                         constexpr int TXT = 16, TY = FLB_MARCH2_TY, NZ = FLB_MARCH_NZ;
                         const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                         const dim3 b(TXT, TY, 1);

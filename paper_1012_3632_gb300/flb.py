@@ -35,6 +35,7 @@ EXPORTS = [
     "flb_batch_create", "flb_batch_init", "flb_batch_step", "flb_batch_autotune", "flb_batch_mode_variance",
     "flb_batch_structure_factor", "flb_batch_get_populations", "flb_batch_info", "flb_batch_synchronize",
     "flb_batch_destroy", "flb_get_state_device", "flb_set_state_device", "flb_adjoint_step",
+    "flb_interface_heights", "flb_height_spectrum",
 ]
 BATCH_MAX = 96
 NOALLOC_MAX_SITES = 1 << 20
@@ -48,7 +49,33 @@ class FLBError(RuntimeError):
 
 class FreeEnergy(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int), ("A", ctypes.c_double), ("B", ctypes.c_double),
-                ("rho_c", ctypes.c_double), ("kappa", ctypes.c_double)]
+                ("rho_c", ctypes.c_double), ("kappa", ctypes.c_double), ("total", ctypes.c_int)]
+
+
+class InterfaceFit(ctypes.Structure):
+    _fields_ = [("rho_l", ctypes.c_double), ("rho_v", ctypes.c_double), ("width", ctypes.c_double),
+                ("guess", ctypes.c_double * 2), ("window", ctypes.c_int), ("iterations", ctypes.c_int)]
+
+
+def interface_fit(rho_l: float, rho_v: float, width: float, guess, window: int = 8,
+                  iterations: int = 8) -> InterfaceFit:
+    """flb_interface_fit for a stripe with interfaces near rows guess = (lower, upper)."""
+    return InterfaceFit(float(rho_l), float(rho_v), float(width), (ctypes.c_double * 2)(*map(float, guess)),
+                        int(window), int(iterations))
+
+
+def landau_width(rho_l: float, rho_v: float, beta: float, kappa: float) -> float:
+    """Interface width w = sqrt(8 kappa / beta) / (rho_L - rho_V) of the mean-field
+    profile of the Landau double well (Sec. VI, Eq. (interf-width))."""
+    return (8.0 * kappa / beta) ** 0.5 / (rho_l - rho_v)
+
+
+def landau_free_energy(rho_l: float, rho_v: float, beta: float, kappa: float) -> dict:
+    """Free-energy parameters of the Landau double well beta (rho - rho_V)^2 (rho - rho_L)^2
+    of Sec. VI as the total bulk free energy: psi' = A d + B d^3, d = rho - (rho_L + rho_V)/2,
+    with A = -beta (rho_L - rho_V)^2 and B = 4 beta."""
+    return dict(A=-beta * (rho_l - rho_v) ** 2, B=4.0 * beta, rho_c=0.5 * (rho_l + rho_v), kappa=kappa,
+                total=True)
 
 
 class Options(ctypes.Structure):
@@ -109,6 +136,8 @@ def lib():
         "flb_get_state_device": (ctypes.c_int, [vp, vp]),
         "flb_set_state_device": (ctypes.c_int, [vp, vp]),
         "flb_adjoint_step": (ctypes.c_int, [vp, vp, ctypes.c_uint64, vp, vp, vp]),
+        "flb_interface_heights": (ctypes.c_int, [vp, P(InterfaceFit), dp]),
+        "flb_height_spectrum": (ctypes.c_int, [vp, P(InterfaceFit), dp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -161,10 +190,11 @@ class Context:
         else:
             dims = list(dims) + [1] * (3 - len(dims))
             d = (ctypes.c_int * 3)(*dims)
-            fe = FreeEnergy(0, 0.0, 0.0, 1.0, 0.0)
+            fe = FreeEnergy(0, 0.0, 0.0, 1.0, 0.0, 0)
             if free_energy:
                 fe = FreeEnergy(1, free_energy.get("A", 0.0), free_energy.get("B", 0.0),
-                                free_energy.get("rho_c", 1.0), free_energy.get("kappa", 0.0))
+                                free_energy.get("rho_c", 1.0), free_energy.get("kappa", 0.0),
+                                int(bool(free_energy.get("total", False))))
             o = options(**opts)
             h = ctypes.c_void_p()
             _check(L.flb_create(ctypes.byref(h), lattice, d, omega_shear, omega_bulk, omega_ghost, kT,
@@ -243,6 +273,18 @@ class Context:
     def structure_factor(self, mode: int = 0, accumulate: bool = False, fetch: bool = True):
         S = np.empty(self.V) if fetch else None
         _check(lib().flb_structure_factor(self._h, None if S is None else _dptr(S), mode, int(bool(accumulate))))
+        return S
+
+    def interface_heights(self, fit: InterfaceFit) -> np.ndarray:
+        """(2, X) heights of the lower and upper interface of a D2Q9 stripe."""
+        h = np.empty(2 * self.dims[0])
+        _check(lib().flb_interface_heights(self._h, ctypes.byref(fit), _dptr(h)))
+        return h.reshape(2, -1)
+
+    def height_spectrum(self, fit: InterfaceFit, accumulate: bool = False, fetch: bool = True):
+        S = np.empty(self.dims[0]) if fetch else None
+        _check(lib().flb_height_spectrum(self._h, ctypes.byref(fit), None if S is None else _dptr(S),
+                                         int(bool(accumulate))))
         return S
 
     def snapshot_count(self, mode: int) -> int:

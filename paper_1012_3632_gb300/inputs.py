@@ -55,3 +55,21 @@ def replica_sizes(n: int = 64, choices=(32, 48, 64, 96, 128), seed: int = 4) -> 
 def replica_omegas(n: int = 64, lo: float = 0.8, hi: float = 1.6, seed: int = 4) -> np.ndarray:
     rng = np.random.default_rng(seed + 1)
     return rng.uniform(lo, hi, n)
+
+
+def stripe_density(X: int, Y: int, rho_l: float, rho_v: float, width: float, y_lo: float, y_hi: float,
+                   amp: float = 0.0, modes: int = 0, seed: int = 6) -> np.ndarray:
+    """(Y, X) density of a liquid stripe between rows y_lo and y_hi: two tanh
+    interfaces of width `width` between rho_v and rho_l.  With modes > 0 each
+    interface is displaced by a sum of `modes` random long-wave sines of total
+    amplitude ~amp (seeded)."""
+    rng = np.random.default_rng(seed)
+    x = np.arange(X)
+    h = np.zeros((2, X))
+    for i in range(2):
+        for n in range(1, modes + 1):
+            h[i] += amp / np.sqrt(modes) * rng.standard_normal() * np.sin(2 * np.pi * n * x / X + rng.uniform(0, 2 * np.pi))
+    y = np.arange(Y)[:, None]
+    a = 0.5 * (rho_l - rho_v)
+    return rho_v + a * (np.tanh(2 * (y - (y_lo + h[0])[None, :]) / width) - np.tanh(2 * (y - (y_hi + h[1])[None, :]) / width))
+

@@ -30,13 +30,18 @@ def _g0(dims, seed=3, amp=0.01, thermal=False, kT=1e-6):
     return f0 - oracle.lattice(19).w[:, None]
 
 
-@pytest.mark.parametrize("nonideal", [True, False])
-def test_adjoint_equals_autograd_reference(nonideal):
+# Landau double well of Sec. VI (rho_L = 1, rho_V = 0.5, beta = 0.1, kappa = 0.08) as total free energy
+LANDAU = dict(A=-0.025, B=0.4, rho_c=0.75, kappa=0.08)
+
+
+@pytest.mark.parametrize("nonideal,total", [(True, False), (False, False), (True, True)])
+def test_adjoint_equals_autograd_reference(nonideal, total):
     dims, nsteps = (6, 5, 4), 8
-    theta0 = [1.2, 0.9, 1.3, FE["kappa"], FE["A"], FE["B"]]
+    fe = LANDAU if total else FE
+    theta0 = [1.2, 0.9, 1.3, fe["kappa"], fe["A"], fe["B"]]
     kT, seed = 1e-4, 7
     p = oracle.Params(Q=19, dims=dims, omega_shear=theta0[0], omega_bulk=theta0[1], omega_ghost=theta0[2], kT=kT,
-                      seed=seed, nonideal=nonideal, **FE)
+                      seed=seed, nonideal=nonideal, total=total, **fe)
     g0 = _g0(dims, seed=2, amp=0.02, thermal=True, kT=kT)
     X, Y, Z = dims
     # reference
@@ -47,7 +52,7 @@ def test_adjoint_equals_autograd_reference(nonideal):
     density_spectrum_loss(gN_ref.reshape(19, -1), dims).backward()
     # GPU adjoint, checkpoints every 3 steps
     cfg = dict(dims=dims, kT=kT, seed=seed, precision="fp64", nsteps=nsteps, every=3, nonideal=nonideal,
-               rho_c=FE["rho_c"])
+               rho_c=fe["rho_c"], total=total)
     gd = torch.tensor(g0, device="cuda", requires_grad=True)
     td = torch.tensor(theta0, dtype=torch.float64, requires_grad=True)
     gN = run(gd, td, cfg)
