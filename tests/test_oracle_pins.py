@@ -538,3 +538,68 @@ def test_structure_factor_matches_numpy(orc):
         d = (m[a] - m[a].mean()).reshape(4, 5, 6)
         want = np.abs(np.fft.fftn(d)) ** 2 / p.V
         assert np.allclose(orc.structure_factor(p, f, a).reshape(4, 5, 6), want, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Modified-equilibrium (Swift) model, Sec. IV.C
+# --------------------------------------------------------------------------
+
+def _swift_lbe(L, k, om, cs2k):
+    """Linear LBE of the modified-equilibrium model in moment space (Eq. (lbe-mom)
+    with the equilibrium of Eq. (meq-yeo)): one step m -> A^LB(k) C m."""
+    d = theory.swift_d(cs2k)
+    Om = np.diag(om)
+    E = np.zeros((9, 9))
+    E[0, 0] = E[1, 1] = E[2, 2] = 1.0
+    E[3, 0], E[8, 0] = d, -d
+    C = np.eye(9) - Om @ (np.eye(9) - E)
+    A = L.T @ np.diag(np.exp(-1j * (L.c[:, :2] @ k))) @ L.Tinv
+    return A, A @ C
+
+
+def test_swift_noise_from_fdt(orc):
+    """Eq. (dbe-fdt) with the operator of Eq. (FDBE-yeo) and G of Eq. (f-correl-yeo)
+    gives the noise of Eq. (noise-yeo) with 6 (c_s^2(k) - cs^2)(lambda_e + lambda_eps)
+    in the (e, eps) corners; zero rows and columns for mass and momentum."""
+    L = orc.lattice(9)
+    rng = np.random.default_rng(4)
+    for _ in range(8):
+        k = rng.uniform(-np.pi, np.pi, 2)
+        le, ls, lq, lp = rng.uniform(0.2, 3.0, 4)
+        lam = np.diag([0, 0, 0, le, ls, ls, lq, lq, lp]).astype(complex)
+        cs2k = rng.uniform(0.03, 0.6)
+        Xi = theory.fdt_noise(theory.L_swift(L, k, lam, cs2k), theory.G_swift(L, 1.0, 1e-5, cs2k))
+        want = theory.noise_swift(L, 1.0, 1e-5, le, ls, lq, lp, cs2k)
+        assert np.allclose(Xi, want, rtol=0, atol=1e-12 * np.abs(want).max())
+        tiny = 1e-12 * np.abs(want).max()
+        assert np.allclose(Xi[:3], 0, atol=tiny) and np.allclose(Xi[:, :3], 0, atol=tiny)
+        printed = want.copy()
+        printed[3, 8] *= 2
+        printed[8, 3] *= 2
+        assert not np.allclose(Xi, printed, atol=1e-3 * np.abs(want).max())
+    # the ideal gas (c_s^2(k) = cs^2) recovers Eq. (noise-ideal)
+    X0 = theory.noise_swift(L, 1.0, 1e-5, 1.1, 0.7, 1.3, 0.9, CS2)
+    lam0 = np.array([0, 0, 0, 1.1, 0.7, 0.7, 1.3, 1.3, 0.9])
+    assert np.allclose(X0, np.diag(2 * lam0 * 1.0 * 1e-5 / CS2 * L.N), rtol=1e-14, atol=0)
+
+
+def test_swift_lattice_noise_is_exactly_stationary(orc):
+    """The lattice noise built from Eq. (noise-yeo) by the Sec. V map
+    (xi^LB = (1 - omega/2) xi, lambda = 2 omega / (2 - omega)) makes the covariance
+    G of Eq. (f-correl-yeo) the exact stationary covariance of the linear LBE:
+    G = M G M^dagger + A Xi^LB A^dagger, M = A^LB(k) C, for any k and rates."""
+    from scipy.linalg import solve_discrete_lyapunov
+
+    L = orc.lattice(9)
+    rng = np.random.default_rng(6)
+    for _ in range(6):
+        k = rng.uniform(-np.pi, np.pi, 2)
+        oe, os_, oq, op = rng.uniform(0.3, 1.8, 4)
+        om = np.array([0, 0, 0, oe, os_, os_, oq, oq, op])
+        _, K2 = theory.stencil_symbols(L, k)
+        cs2k = 0.07 + 0.08 * K2
+        A, M = _swift_lbe(L, k, om, cs2k)
+        Xi = theory.swift_lattice_noise(L, 1.0, 1e-5, oe, os_, oq, op, cs2k)
+        G = solve_discrete_lyapunov(M, A @ Xi @ A.conj().T)
+        G0 = theory.G_swift(L, 1.0, 1e-5, cs2k)
+        assert np.allclose(G, G0, rtol=0, atol=1e-10 * np.abs(G0).max())
