@@ -49,6 +49,7 @@ class _Params(ctypes.Structure):
         ("A", ctypes.c_double), ("B", ctypes.c_double), ("rho_c", ctypes.c_double),
         ("kappa", ctypes.c_double),
         ("total", ctypes.c_int),
+        ("model", ctypes.c_int),
         ("seed", ctypes.c_uint64),
         ("replica", ctypes.c_uint32),
     ]
@@ -74,6 +75,7 @@ class Params:
     rho_c: float = 1.0
     kappa: float = 0.0
     total: bool = False
+    model: int = 0  # 0 force-based, 1 modified equilibrium (D2Q9)
     seed: int = 1
     replica: int = 0
     origin: tuple = (0, 0, 0)
@@ -99,7 +101,7 @@ class Params:
         return _Params(self.Q, X, Y, Z, ox, oy, oz, wx, wy, wz,
                        self.omega_shear, self.omega_bulk, self.omega_ghost,
                        self.kT, self.rho0, int(self.noise_rho_local), int(self.nonideal),
-                       self.A, self.B, self.rho_c, self.kappa, int(self.total),
+                       self.A, self.B, self.rho_c, self.kappa, int(self.total), int(self.model),
                        self.seed & 0xFFFFFFFFFFFFFFFF, self.replica & 0xFFFFFFFF)
 
     def with_(self, **kw) -> "Params":

@@ -81,6 +81,7 @@ typedef struct {
     int nonideal;
     double A, B, rho_c, kappa;   /* psi(rho) = A (rho-rho_c)^2/2 + B (rho-rho_c)^4/4 */
     int total;                   /* psi is the total bulk free energy f0 of App. A */
+    int model;                   /* 0: force-based (App. A); 1: modified equilibrium (Sec. IV.C, D2Q9) */
     uint64_t seed;
     uint32_t replica;
 } orc_params;
@@ -316,6 +317,9 @@ static int check_params(const orc_params* p, orc_lattice* L)
     if (p->X < 1 || p->Y < 1 || p->Z < 1 || p->wx < 1 || p->wy < 1 || p->wz < 1) return -1;
     if (p->wx > p->X || p->wy > p->Y || p->wz > p->Z) return -1;
     if (p->Q == 9 && p->Z != 1) return -1;
+    if (p->nonideal && p->model == 1 &&
+        (p->Q != 9 || p->wx != p->X || p->wy != p->Y || p->wz != p->Z))
+        return -1; /* modified equilibrium: D2Q9, full lattice (its noise lives in k-space) */
     return 0;
 }
 
@@ -358,8 +362,10 @@ static void forcing(const orc_lattice* L, const double u[3], const double F[3], 
 
 /* One site of Eq. (lbe-mom): f (pre-collision f^LB) -> fstar (post-collision),
  * before streaming.  F is the body force at the site; site/step key the noise. */
+/* sw (modified-equilibrium model only, else NULL): {p - rho s2, d_x rho,
+ * d_y rho, xi_e, xi_eps} at the site; see swift_fields(). */
 static void collide(const orc_params* p, const orc_lattice* L, const double f[], const double F[3],
-                    uint32_t site, uint64_t step, double fstar[])
+                    uint32_t site, uint64_t step, const double* sw, double fstar[])
 {
     int Q = L->Q;
     double m[ORC_QMAX], meq[ORC_QMAX], mF[ORC_QMAX], ms[ORC_QMAX];
@@ -389,6 +395,16 @@ static void collide(const orc_params* p, const orc_lattice* L, const double f[],
             mF[a] += L->T[a][i] * phi[i];
         }
     }
+    if (sw) {
+        /* Eq. (meq-yeo) with the pressure p = p0(rho) - kappa rho lap rho and the
+         * square-gradient stress kappa (d_a rho d_b rho - |grad rho|^2 delta_ab / 2)
+         * in the equilibrium: e gets 6 (p - rho s2), eps gets -6 (p - rho s2),
+         * p_ww and p_xy the deviatoric stress.  D2Q9 mode order of App. B. */
+        meq[3] += 6.0 * sw[0];
+        meq[8] -= 6.0 * sw[0];
+        meq[4] += p->kappa * (sw[1] * sw[1] - sw[2] * sw[2]);
+        meq[5] += p->kappa * sw[1] * sw[2];
+    }
 
     double rho_n = p->noise_rho_local ? rho : p->rho0;
     double z[ORC_QMAX];
@@ -401,6 +417,9 @@ static void collide(const orc_params* p, const orc_lattice* L, const double f[],
             /* Eq. (noise-lbe): variance rho kT (2-omega) omega N_a / s2, Delta V = 1 */
             double var = rho_n * p->kT * (2.0 - om) * om * L->N[a] / S2;
             xi = sqrt(var) * z[k];
+            /* modified equilibrium: e and eps carry the k-dependent noise */
+            if (sw && a == 3) xi = sw[3];
+            if (sw && a == 8) xi = sw[4];
             k++;
         }
         ms[a] = m[a] - om * (m[a] - meq[a]) + (1.0 - 0.5 * om) * mF[a] + xi;
@@ -419,7 +438,7 @@ int orc_collide_site(const orc_params* p, const double* f, const double* F, uint
     orc_lattice L;
     if (lattice_of(p->Q, &L)) return -1;
     double F3[3] = {F[0], F[1], L.D == 3 ? F[2] : 0.0};
-    collide(p, &L, f, F3, site, step, fstar);
+    collide(p, &L, f, F3, site, step, NULL, fstar);
     return 0;
 }
 
@@ -451,7 +470,7 @@ static void density_force(const orc_params* p, const orc_lattice* L, const doubl
         for (int i = 0; i < L->Q; i++) rho[s] += f[i * V + s];
         F[s] = F[V + s] = F[2 * V + s] = 0.0;
     }
-    if (!p->nonideal) return;
+    if (!p->nonideal || p->model == 1) return;
 
     double* mu = (double*)malloc(sizeof(double) * V);
     for (int z = 0; z < p->wz; z++)
@@ -502,6 +521,157 @@ int orc_density_force(const orc_params* p, const double* f, double* rho, double*
 /* Time step, Eq. (lbe-gen) / (lbe-mom): collide at r, move to r + c_i  */
 /* ------------------------------------------------------------------ */
 
+int orc_dft(int nx, int ny, int nz, const double* phi, double* out_re, double* out_im);
+
+/* ------------------------------------------------------------------ */
+/* Modified-equilibrium model (Sec. IV.C), D2Q9                          */
+/* ------------------------------------------------------------------ */
+
+/* Bulk pressure minus the ideal lattice-gas pressure, p0(rho) - rho s2, with
+ * p0 = rho psi' - psi (+ rho s2 when psi is the excess free energy). */
+static double p0_excess(const orc_params* p, double rho)
+{
+    double d = rho - p->rho_c;
+    double psi = 0.5 * p->A * d * d + 0.25 * p->B * d * d * d * d;
+    double v = rho * psi_prime(p, rho) - psi;
+    return p->total ? v - rho * S2 : v;
+}
+
+/* c_s^2 = d p0 / d rho at rho0 (the speed of sound of Eq. (s-nonideal)). */
+static double cs2_rho0(const orc_params* p)
+{
+    double d = p->rho0 - p->rho_c;
+    double psi2 = p->A + 3.0 * p->B * d * d;
+    return p->rho0 * psi2 + (p->total ? 0.0 : S2);
+}
+
+/* In-place inverse DFT of a complex nx*ny field: phi(r) = (1/V) sum_k phi(k) e^{ik.r},
+ * direct sums along x, then y. */
+static void idft2(int nx, int ny, double* re, double* im)
+{
+    int n[2] = {nx, ny};
+    long stride[2] = {1, nx};
+    long V = (long)nx * ny;
+    int Lmax = nx > ny ? nx : ny;
+    double* lr = (double*)malloc(sizeof(double) * Lmax);
+    double* li = (double*)malloc(sizeof(double) * Lmax);
+    for (int ax = 0; ax < 2; ax++) {
+        int L = n[ax];
+        if (L == 1) continue;
+        for (long base = 0; base < V; base++) {
+            if ((base / stride[ax]) % L != 0) continue;
+            for (int r = 0; r < L; r++) {
+                double a = 0, b = 0;
+                for (int k = 0; k < L; k++) {
+                    double t = 2.0 * ORC_PI * (double)(((long)k * r) % L) / L;
+                    double x = re[base + k * stride[ax]], y = im[base + k * stride[ax]];
+                    a += x * cos(t) - y * sin(t); /* (x + iy)(cos + i sin) */
+                    b += x * sin(t) + y * cos(t);
+                }
+                lr[r] = a;
+                li[r] = b;
+            }
+            for (int r = 0; r < L; r++) {
+                re[base + r * stride[ax]] = lr[r];
+                im[base + r * stride[ax]] = li[r];
+            }
+        }
+    }
+    for (long s = 0; s < V; s++) {
+        re[s] /= V;
+        im[s] /= V;
+    }
+    free(lr);
+    free(li);
+}
+
+/* Per-site inputs of the modified-equilibrium collision, sw[5 s + 0..4] =
+ * {p - rho s2, d_x rho, d_y rho, xi_e, xi_eps}:
+ *   p = p0(rho) - kappa rho lap rho (isotropic stencils);
+ *   (xi_e, xi_eps): Gaussian field with, at each k = 2 pi n / L, the 2x2
+ *   covariance of the e and eps modes of the lattice noise (Eq. (noise-yeo)
+ *   under the map of Sec. V: xi^LB = (1 - omega/2) xi, lambda = 2 omega/(2 - omega)),
+ *   c_s^2(k) = c_s^2 + kappa rho0 K2(k), K2(k) = (2/s2) sum_i w_i (1 - cos k.c_i),
+ *   made from the white normals z_e, z_eps of the collision draw (modes e and
+ *   eps, i.e. normals 0 and 5 of the site) by xi(k) = C(k) z(k), C C^T the
+ *   covariance (lower Cholesky factor), and an inverse DFT.
+ * Returns -1 where the covariance is not positive definite. */
+static int swift_fields(const orc_params* p, const orc_lattice* L, const double* rho, uint64_t step, double* sw)
+{
+    int X = p->X, Y = p->Y;
+    long V = (long)X * Y;
+    for (int y = 0; y < Y; y++)
+        for (int x = 0; x < X; x++) {
+            long s = x + (long)X * y;
+            double lap = 0, g[2] = {0, 0};
+            for (int i = 0; i < L->Q; i++) {
+                long n = nbr(p, x, y, 0, L->c[i][0], L->c[i][1], 0);
+                lap += L->w[i] * (rho[n] - rho[s]);
+                for (int d = 0; d < 2; d++) g[d] += L->w[i] * L->c[i][d] * rho[n];
+            }
+            lap *= 2.0 / S2;
+            sw[5 * s + 0] = p0_excess(p, rho[s]) - p->kappa * rho[s] * lap;
+            sw[5 * s + 1] = g[0] / S2;
+            sw[5 * s + 2] = g[1] / S2;
+            sw[5 * s + 3] = sw[5 * s + 4] = 0.0;
+        }
+    if (p->kT == 0.0) return 0;
+
+    double* er = (double*)malloc(sizeof(double) * V);
+    double* ei = (double*)malloc(sizeof(double) * V);
+    double* pr = (double*)malloc(sizeof(double) * V);
+    double* pi = (double*)malloc(sizeof(double) * V);
+    double* ze = (double*)malloc(sizeof(double) * V);
+    double* zp = (double*)malloc(sizeof(double) * V);
+    for (int y = 0; y < Y; y++)
+        for (int x = 0; x < X; x++) {
+            double z[8];
+            normals(p, global_site(p, x, y, 0), step, 0, L->Q - 1 - L->D, z);
+            ze[x + (long)X * y] = z[0];
+            zp[x + (long)X * y] = z[5];
+        }
+    orc_dft(X, Y, 1, ze, er, ei);
+    orc_dft(X, Y, 1, zp, pr, pi);
+    double oe = p->omega_bulk, op = p->omega_ghost;
+    double le = 2.0 * oe / (2.0 - oe), lp = 2.0 * op / (2.0 - op);
+    double se = 1.0 - 0.5 * oe, sp = 1.0 - 0.5 * op;
+    double pre = 2.0 * p->rho0 * p->kT / S2, cs2 = cs2_rho0(p);
+    int bad = 0;
+    for (int ny = 0; ny < Y; ny++)
+        for (int nx = 0; nx < X; nx++) {
+            long s = nx + (long)X * ny;
+            double kx = 2.0 * ORC_PI * nx / X, ky = 2.0 * ORC_PI * ny / Y, K2 = 0;
+            for (int i = 0; i < L->Q; i++) K2 += L->w[i] * (1.0 - cos(kx * L->c[i][0] + ky * L->c[i][1]));
+            K2 *= 2.0 / S2;
+            double c2 = cs2 + p->kappa * p->rho0 * K2;
+            double a = se * se * pre * L->N[3] * (2.0 - 3.0 * c2) * le;
+            double c = sp * sp * pre * L->N[8] * (1.25 - 0.75 * c2) * lp;
+            double b = se * sp * pre * 6.0 * (c2 - S2) * (le + lp);
+            if (!(a > 0) || !(c - b * b / a >= 0)) bad = 1;
+            double c11 = sqrt(a > 0 ? a : 0), c21 = a > 0 ? b / c11 : 0;
+            double c22 = sqrt(c - c21 * c21 > 0 ? c - c21 * c21 : 0);
+            double e_r = c11 * er[s], e_i = c11 * ei[s];
+            double p_r = c21 * er[s] + c22 * pr[s], p_i = c21 * ei[s] + c22 * pi[s];
+            er[s] = e_r;
+            ei[s] = e_i;
+            pr[s] = p_r;
+            pi[s] = p_i;
+        }
+    idft2(X, Y, er, ei);
+    idft2(X, Y, pr, pi);
+    for (long s = 0; s < V; s++) {
+        sw[5 * s + 3] = er[s];
+        sw[5 * s + 4] = pr[s];
+    }
+    free(er);
+    free(ei);
+    free(pr);
+    free(pi);
+    free(ze);
+    free(zp);
+    return bad ? -1 : 0;
+}
+
 int orc_step(const orc_params* p, uint64_t step, const double* f, double* fnew)
 {
     orc_lattice L;
@@ -512,6 +682,16 @@ int orc_step(const orc_params* p, uint64_t step, const double* f, double* fnew)
     double* F = (double*)malloc(sizeof(double) * 3 * V);
     density_force(p, &L, f, rho, F);
     for (long n = 0; n < (long)Q * V; n++) fnew[n] = NAN; /* sites fed from outside the window */
+    double* sw = NULL;
+    if (p->nonideal && p->model == 1) {
+        sw = (double*)malloc(sizeof(double) * 5 * V);
+        if (swift_fields(p, &L, rho, step, sw)) {
+            free(sw);
+            free(rho);
+            free(F);
+            return -1;
+        }
+    }
 
     for (int z = 0; z < p->wz; z++)
         for (int y = 0; y < p->wy; y++)
@@ -520,12 +700,13 @@ int orc_step(const orc_params* p, uint64_t step, const double* f, double* fnew)
                 double fs[ORC_QMAX], fst[ORC_QMAX], Fs[3];
                 for (int i = 0; i < Q; i++) fs[i] = f[i * V + s];
                 for (int d = 0; d < 3; d++) Fs[d] = F[d * V + s];
-                collide(p, &L, fs, Fs, global_site(p, x, y, z), step, fst);
+                collide(p, &L, fs, Fs, global_site(p, x, y, z), step, sw ? sw + 5 * s : NULL, fst);
                 for (int i = 0; i < Q; i++) {
                     long n = nbr(p, x, y, z, L.c[i][0], L.c[i][1], L.c[i][2]);
                     if (n >= 0) fnew[i * V + n] = fst[i];
                 }
             }
+    free(sw);
     free(rho);
     free(F);
     return 0;

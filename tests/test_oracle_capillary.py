@@ -141,3 +141,60 @@ def test_capillary_spectrum_continuum_limit():
     sig = cap.surface_tension(RL, RV, BETA, KAPPA)
     k = np.array([1e-3, 1e-2])
     assert np.allclose(cap.capillary_spectrum(k, 1e-7, sig), 1e-7 / (sig * k ** 2), rtol=1e-4)
+
+
+# --------------------------------------------------------------------------
+# Modified-equilibrium (Swift) model, Sec. IV.C
+# --------------------------------------------------------------------------
+
+def test_swift_stripe_keeps_the_mean_field_interface(orc):
+    """With the non-ideal pressure in the equilibrium (Eq. (meq-yeo) plus the
+    square-gradient stress) and kT = 0, the D2Q9 stripe started from the
+    mean-field profile stays on it: fitted width within 3 % of Eq. (interf-width),
+    bulk densities within 1e-3 of rho_L and rho_V, interfaces fixed, velocities
+    vanishing (mechanical equilibrium reduces to mu = const, as in the continuum)."""
+    from scipy.optimize import least_squares
+
+    from paper_1012_3632_gb300 import inputs
+
+    X, Y = 4, 64
+    w = cap.width(RL, RV, BETA, KAPPA)
+    p = orc.Params(Q=9, dims=(X, Y, 1), nonideal=True, kappa=KAPPA, total=True, model=1, **cap.landau(RL, RV, BETA))
+    f = orc.run(p, orc.init(p, rho=inputs.stripe_density(X, Y, RL, RV, w, 16.0, 48.0)), 0, 4000)
+    rho = f.sum(axis=0).reshape(Y, X)[:, 0]
+    ys = np.arange(4, 28)
+    fit = least_squares(lambda q: rho[ys] - (0.5 * (q[2] + q[3]) + 0.5 * (q[2] - q[3]) * np.tanh(2 * (ys - q[0]) / q[1])),
+                        [16.0, 5.0, 1.0, 0.5]).x
+    assert abs(fit[1] / w - 1) < 0.03
+    assert abs(fit[0] - 16.0) < 0.05
+    assert abs(rho[32] - RL) < 1e-3 and abs(rho[0] - RV) < 1e-3
+    assert np.abs(orc.velocity(p, f)).max() < 1e-8
+
+
+def test_swift_modes_equilibrate_to_the_modified_equilibrium_covariance(orc):
+    """Homogeneous Landau liquid (rho0 = 1, c_s^2 = 0.05) of the modified-equilibrium
+    model with the k-dependent noise: every mode's <|dm_a(k)|^2>/V, averaged over
+    k != 0, equals G_aa(k) of Eq. (f-correl-yeo) within 3 % (300 snapshots)."""
+    from oracle import theory
+
+    N = 16
+    p = orc.Params(Q=9, dims=(N, N, 1), nonideal=True, kappa=KAPPA, total=True, model=1, kT=1e-6,
+                   omega_shear=1.0, omega_bulk=1.1, omega_ghost=1.2, seed=5, **cap.landau(RL, RV, BETA))
+    L = orc.lattice(9)
+    f = orc.run(p, orc.init(p, rho=np.ones(N * N)), 0, 2000)
+    acc = np.zeros((9, N * N))
+    t = 2000
+    for _ in range(300):
+        f = orc.run(p, f, t, 10)
+        t += 10
+        for a in range(9):
+            acc[a] += orc.structure_factor(p, f, a)
+    acc /= 300
+    k1 = 2 * np.pi * np.fft.fftfreq(N)
+    G = np.zeros((9, N * N))
+    for iy in range(N):
+        for ix in range(N):
+            _, K2 = theory.stencil_symbols(L, np.array([k1[ix], k1[iy]]))
+            G[:, ix + N * iy] = np.diag(theory.G_swift(L, 1.0, 1e-6, 0.05 + KAPPA * K2)).real
+    ratio = (acc[:, 1:] / G[:, 1:]).mean(axis=1)
+    assert np.all(np.abs(ratio - 1) < 0.03), ratio
