@@ -111,6 +111,18 @@ typedef struct {
     int enabled;
     double A, B, rho_c, kappa;
     int total;
+    int model;  /* 0: force-based model (App. A, above); 1: modified-equilibrium
+                   model (Sec. IV.C), D2Q9 only: no force; the equilibrium carries
+                   the pressure p = p0(rho) - kappa rho lap rho in e and eps
+                   (Eq. (meq-yeo): e += 6 (p - rho cs^2), eps = -6 (p - rho cs^2)) and
+                   the square-gradient stress kappa (d_a rho d_b rho - |grad rho|^2
+                   delta_ab / 2) in p_ww and p_xy, with p0 = rho psi' - psi
+                   (+ rho cs^2 when total = 0); the e and eps noise is drawn in
+                   Fourier space with the k-dependent covariance of Eq. (noise-yeo)
+                   (corner 6 (c_s^2(k) - cs^2)(lambda_e + lambda_eps), from the FDT)
+                   mapped to the lattice as in Sec. V, c_s^2(k) = dp0/drho(rho0) +
+                   kappa rho0 K2(k) with K2 the symbol of -lap; flb_create fails
+                   with FLB_EINVAL where that covariance is not positive definite. */
 } flb_free_energy;
 
 typedef struct {

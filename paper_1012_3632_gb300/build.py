@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libflb.so")
-SOURCES = ["flb_api.cu", "flb_fp64.cu", "flb_fp32.cu", "flb_bf16.cu", "flb_fft.cu", "flb_noalloc.cu", "flb_batch.cu", "flb_adjoint.cu", "flb_capillary.cu"]
+SOURCES = ["flb_api.cu", "flb_fp64.cu", "flb_fp32.cu", "flb_bf16.cu", "flb_fft.cu", "flb_noalloc.cu", "flb_batch.cu", "flb_adjoint.cu", "flb_capillary.cu", "flb_swift.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -18,12 +18,13 @@ from .flb import D2Q9, Context, interface_fit, landau_free_energy, landau_width
 
 
 def stripe_context(X=1024, Y=400, thickness=200, rho_l=1.0, rho_v=0.5, beta=0.1, kappa=0.08, kT=1e-7,
-                   omega=1.0, seed=11, precision="fp32", stream=None):
-    """Context holding the mean-field stripe centred in y; returns (ctx, fit)."""
+                   omega=1.0, seed=11, precision="fp32", stream=None, model=0):
+    """Context holding the mean-field stripe centred in y; returns (ctx, fit).
+    model 0: force-based fluid (App. A); model 1: modified equilibrium (Sec. IV.C)."""
     w = landau_width(rho_l, rho_v, beta, kappa)
     y_lo, y_hi = 0.5 * (Y - thickness), 0.5 * (Y + thickness)
-    ctx = Context(D2Q9, (X, Y, 1), omega, omega, omega, kT=kT,
-                  free_energy=landau_free_energy(rho_l, rho_v, beta, kappa), seed=seed, precision=precision,
+    fe = dict(landau_free_energy(rho_l, rho_v, beta, kappa), model=model)
+    ctx = Context(D2Q9, (X, Y, 1), omega, omega, omega, kT=kT, free_energy=fe, seed=seed, precision=precision,
                   stream=stream)
     ctx.init(rho=inputs.stripe_density(X, Y, rho_l, rho_v, w, y_lo, y_hi).ravel())
     return ctx, interface_fit(rho_l, rho_v, w, (y_lo, y_hi))

@@ -84,6 +84,11 @@ struct flb_ctx {
     std::vector<double> mv_sum;         // per-mode sum over snapshots of the site variance
     int mv_count = 0;
 
+    // modified-equilibrium model: Cholesky table and the two noise fields
+    double* sw_chol = nullptr;
+    double2* sw_work = nullptr;
+    double2* sw_xi = nullptr;
+
     // interface heights and height spectrum of a stripe
     double* h_dev = nullptr;            // 2 X heights
     double2* hs_work = nullptr;         // 2 X complex
@@ -127,7 +132,7 @@ void free_all(flb_ctx* c)
 {
     void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
                     c->adj_work, c->adj_rows, c->adj_col, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
-                    c->hs_tmp};
+                    c->hs_tmp, c->sw_chol, c->sw_work, c->sw_xi};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (double* p : c->sk_acc)
@@ -238,6 +243,9 @@ int validate(int lattice, const int dims[3], double om_s, double om_b, double om
         for (double x : v)
             if (!std::isfinite(x)) return fail(FLB_EINVAL, "free-energy parameters must be finite");
         if (fe->kappa < 0.0) return fail(FLB_EINVAL, "kappa must be >= 0");
+        if (fe->model != 0 && fe->model != 1) return fail(FLB_EINVAL, "free-energy model must be 0 or 1");
+        if (fe->model == 1 && lattice != FLB_D2Q9)
+            return fail(FLB_EINVAL, "the modified-equilibrium model is defined for D2Q9 only");
     }
     return FLB_OK;
 }
@@ -309,6 +317,7 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
         m.rho_c = fe->rho_c;
         m.kappa = fe->kappa;
         m.total = fe->total ? 1 : 0;
+        m.model = fe->model;
     } else {
         m.nonideal = 0;
         m.rho_c = o.rho0;
@@ -322,6 +331,29 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
         free_all(c);
         delete c;
         return rc;
+    }
+    if (m.nonideal && m.model == 1 && m.kT > 0.0) {
+        std::vector<double> chol(3 * (size_t)m.V);
+        std::string err;
+        if (!flb::swift_table(m, chol.data(), err)) {
+            free_all(c);
+            delete c;
+            return fail(FLB_EINVAL, err);
+        }
+        if ((rc = alloc((void**)&c->sw_chol, chol.size() * sizeof(double))) ||
+            (rc = alloc((void**)&c->sw_work, m.V * sizeof(double2))) ||
+            (rc = alloc((void**)&c->sw_xi, m.V * sizeof(double2)))) {
+            free_all(c);
+            delete c;
+            return rc;
+        }
+        const cudaError_t ce = cudaMemcpy(c->sw_chol, chol.data(), chol.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            free_all(c);
+            delete c;
+            return fail(FLB_ECUDA, std::string("uploading the noise table: ") + cudaGetErrorString(ce));
+        }
+        m.swift_xi = c->sw_xi;
     }
     // rest state: all deviations zero
     cudaError_t e = cudaMemsetAsync(c->buf[0], 0, c->pop_bytes(), c->stream);
@@ -376,6 +408,7 @@ int flb_step(flb_ctx* c, int nsteps)
         if (c->ops->step_needs_density(c->m)) {
             if ((rc = timer_begin(c, 0, &slot))) return rc;
             FLB_CUDA(c->ops->density(c->m, src, c->drho, c->stream));
+            if (c->sw_xi) FLB_CUDA(flb::swift_noise(c->m, c->step, c->sw_chol, c->sw_work, c->sw_xi, c->stream));
             if ((rc = timer_end(c, slot))) return rc;
         }
         if ((rc = timer_begin(c, 1, &slot))) return rc;
@@ -430,7 +463,7 @@ int flb_moments(flb_ctx* c, double* out, int which)
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     const void* F = nullptr;
-    if (which == FLB_U && m.nonideal) {
+    if (which == FLB_U && m.nonideal && m.model == 0) {
         if ((rc = alloc(&c->mu, c->field_bytes())) || (rc = alloc(&c->F, 3 * c->field_bytes()))) {
             cudaFree(d_out);
             return rc;
@@ -729,7 +762,9 @@ int flb_save(flb_ctx* c, const char* path)
     FILE* fp = std::fopen(path, "wb");
     if (!fp) return fail(FLB_EIO, std::string("cannot open ") + path);
     const HostModel& m = c->m;
-    const int32_t ints[8] = {m.Q, m.X, m.Y, m.Z, c->prec, c->fe.enabled, m.noise_local, 0};
+    // ints[7]: free-energy flags, total | model << 1
+    const int32_t ints[8] = {m.Q, m.X, m.Y, m.Z, c->prec, c->fe.enabled, m.noise_local,
+                             (c->fe.total ? 1 : 0) | (c->fe.model << 1)};
     const double dbl[10] = {m.rho0, m.om_s, m.om_b, m.om_g, m.kT, c->fe.A, c->fe.B, c->fe.rho_c, c->fe.kappa, 0.0};
     const uint64_t u64[3] = {m.seed, (uint64_t)m.replica, c->step};
     bool ok = std::fwrite(kMagic, 1, 8, fp) == 8 && std::fwrite(ints, sizeof(ints), 1, fp) == 1 &&
@@ -763,7 +798,7 @@ int flb_load(flb_ctx** out, const char* path, const flb_options* opt)
     o.rho0 = dbl[0];
     o.replica = (uint32_t)u64[1];
     o.noise_rho_local = ints[6];
-    flb_free_energy fe{ints[5], dbl[5], dbl[6], dbl[7], dbl[8]};
+    flb_free_energy fe{ints[5], dbl[5], dbl[6], dbl[7], dbl[8], ints[7] & 1, (ints[7] >> 1) & 1};
     const int dims[3] = {ints[1], ints[2], ints[3]};
     flb_ctx* c = nullptr;
     int rc = flb_create(&c, ints[0], dims, dbl[1], dbl[2], dbl[3], dbl[4], &fe, u64[0], &o);

@@ -328,6 +328,45 @@ struct D2Q9 {
         }
         add_back(Dm, g);
     }
+
+    // Modified-equilibrium model (Sec. IV.C): no force; the equilibrium adds
+    // pex = p - rho cs^2 to e (x 6) and eps (x -6) (Eq. (meq-yeo)) and the
+    // square-gradient stress kappa (d_a rho d_b rho - |grad rho|^2 delta/2) to
+    // p_ww and p_xy; e and eps take the coloured noise (xe, xp) given per site,
+    // the other non-conserved modes their white noise.
+    template <class R, class PR>
+    __device__ __forceinline__ static void collide_swift(R g[9], R pex, R gx, R gy, R kappa, R xe, R xp,
+                                                         const Coll<PR>& P, uint32_t site, uint32_t step)
+    {
+        R m[9];
+        moments(g, m);
+        const R rho = P.rho0 + m[0];
+        const R ir = rcp_(rho);
+        const R ux = m[1] * ir, uy = m[2] * ir;
+        const R uxx = ux * ux, uyy = uy * uy;
+        const R eq_e = R(3) * rho * (uxx + uyy) + R(6) * pex;
+        const R eq_w = rho * (uxx - uyy) + kappa * (gx * gx - gy * gy);
+        const R eq_xy = rho * ux * uy + kappa * gx * gy;
+        const R eq_eps = R(-6) * pex;
+        R Dm[9];
+        Dm[0] = Dm[1] = Dm[2] = R(0);
+        Dm[3] = P.rel[0] * (m[3] - eq_e);
+        Dm[4] = P.rel[1] * (m[4] - eq_w);
+        Dm[5] = P.rel[2] * (m[5] - eq_xy);
+        Dm[6] = P.rel[3] * m[6];
+        Dm[7] = P.rel[4] * m[7];
+        Dm[8] = P.rel[5] * (m[8] - eq_eps);
+        if (P.noise) {
+            const R sr = P.noise_local ? sqrt_(rho) : R(P.sqrt_rho0);
+            R z[8];
+            noise_normals<2>(P.key, site, step, P.replica, z);
+#pragma unroll
+            for (int k = 1; k < 5; ++k) Dm[3 + k] += P.ns[k] * (sr * z[k]);
+            Dm[3] += xe * R(1.0 / 4.0);   // / N_e
+            Dm[8] += xp * R(1.0 / 16.0);  // / N_eps
+        }
+        add_back(Dm, g);
+    }
 };
 
 // ---------------------------------------------------------------------------

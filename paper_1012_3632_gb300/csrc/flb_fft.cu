@@ -5,6 +5,7 @@
 // Structure factor of mode a (Sec. IV, Eq. (g-correl); Sec. VI equilibration
 // ratios): S_a(k) = |sum_r dm_a(r) exp(-i k.r)|^2 / V, accumulated in double.
 #include <cmath>
+#include <mutex>
 
 #include "flb_internal.h"
 
@@ -85,54 +86,51 @@ struct LineGeom {
 // One Stockham pass (Govindaraju et al., SC'08 formulation): butterfly j of
 // radix R with Ns = product of the radices already applied reads in[j + r L/R],
 // twiddles by exp(-2 pi i r (j mod Ns) / (Ns R)), applies the R-point DFT and
-// writes out[(j / Ns) Ns R + (j mod Ns) + r Ns].
-__device__ __forceinline__ void butterfly(const double2* __restrict__ in, double2* __restrict__ out, int L, int R,
-                                          int Ns, int j)
+// writes out[(j / Ns) Ns R + (j mod Ns) + r Ns].  tw[m] = exp(-2 pi i m / L).
+template <int R>
+__device__ __forceinline__ void butterfly(const double2* __restrict__ in, double2* __restrict__ out,
+                                          const double2* __restrict__ tw, int L, int Ns, int j)
 {
     const int stride = L / R;
     const int k = j % Ns;
-    double2 v[5];
+    double2 v[R];
+#pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
     if (Ns > 1) {
-        double s, c;
-        sincospi(-2.0 * (double)k / (double)(Ns * R), &s, &c);
-        const double2 w1 = make_double2(c, s);
-        double2 w = w1;
-        for (int r = 1; r < R; ++r) {
-            v[r] = cmul(v[r], w);
-            w = cmul(w, w1);
-        }
+        const int step = k * (L / (Ns * R));  // exp(-2 pi i k / (Ns R)) = tw[step]
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * step) % L]);
     }
-    double2 y[5];
-    if (R == 2) {
+    double2 y[R];
+    if constexpr (R == 2) {
         y[0] = cadd(v[0], v[1]);
         y[1] = csub(v[0], v[1]);
-    } else if (R == 4) {
+    } else if constexpr (R == 4) {
         const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
         const double2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
         y[0] = cadd(a, c);
         y[2] = csub(a, c);
         y[1] = make_double2(b.x + d.y, b.y - d.x);  // b - i d
         y[3] = make_double2(b.x - d.y, b.y + d.x);  // b + i d
-    } else if (R == 3) {
+    } else if constexpr (R == 3) {
         const double h = 0.86602540378443864676;  // sqrt(3)/2
         const double2 t = cadd(v[1], v[2]), u = csub(v[1], v[2]);
         y[0] = cadd(v[0], t);
         const double2 m = make_double2(v[0].x - 0.5 * t.x, v[0].y - 0.5 * t.y);
         y[1] = make_double2(m.x + h * u.y, m.y - h * u.x);  // m - i h u
         y[2] = make_double2(m.x - h * u.y, m.y + h * u.x);  // m + i h u
-    } else {  // R == 5: direct 5-point DFT
+    } else {  // R == 5: direct 5-point DFT, exp(-2 pi i m / 5) = tw[m L / 5]
+        const int f = L / 5;
+#pragma unroll
         for (int q = 0; q < 5; ++q) {
-            double2 acc = make_double2(0.0, 0.0);
-            for (int r = 0; r < 5; ++r) {
-                double s, c;
-                sincospi(-2.0 * (double)((q * r) % 5) / 5.0, &s, &c);
-                acc = cadd(acc, cmul(v[r], make_double2(c, s)));
-            }
+            double2 acc = v[0];
+#pragma unroll
+            for (int r = 1; r < 5; ++r) acc = cadd(acc, cmul(v[r], tw[((q * r) % 5) * f]));
             y[q] = acc;
         }
     }
     const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
     for (int r = 0; r < R; ++r) out[base + r * Ns] = y[r];
 }
 
@@ -142,6 +140,12 @@ __global__ void k_fft_lines(double2* __restrict__ data, const FftPlan plan, cons
     const int L = g.L;
     double2* b0 = sm;
     double2* b1 = sm + (long)B * L;
+    double2* tw = sm + 2l * B * L;
+    for (int m = threadIdx.x; m < L; m += blockDim.x) {
+        double s, c;
+        sincospi(-2.0 * (double)m / (double)L, &s, &c);
+        tw[m] = make_double2(c, s);
+    }
     const int i0 = blockIdx.x * B;
     const long o1 = (long)blockIdx.y * g.s_out;
     const int nl = min(B, g.n_in - i0);
@@ -166,7 +170,12 @@ __global__ void k_fft_lines(double2* __restrict__ data, const FftPlan plan, cons
         const int per = L / R;
         for (int t = threadIdx.x; t < nl * per; t += blockDim.x) {
             const int l = t / per, j = t % per;
-            butterfly(cur + l * L, nxt + l * L, L, R, Ns, j);
+            switch (R) {
+            case 2: butterfly<2>(cur + l * L, nxt + l * L, tw, L, Ns, j); break;
+            case 3: butterfly<3>(cur + l * L, nxt + l * L, tw, L, Ns, j); break;
+            case 4: butterfly<4>(cur + l * L, nxt + l * L, tw, L, Ns, j); break;
+            default: butterfly<5>(cur + l * L, nxt + l * L, tw, L, Ns, j); break;
+            }
         }
         __syncthreads();
         Ns *= R;
@@ -215,6 +224,28 @@ bool fft_length_in_place(int L)
     return L == 1 || (L <= 4096 && make_plan(L, p));
 }
 
+// Opt k_fft_lines into the largest dynamic shared memory it uses (two line
+// buffers of B L <= 8192 elements and a twiddle table of L <= 4096 elements),
+// once per device.
+static cudaError_t fft_smem_optin()
+{
+    constexpr int kMaxDev = 128;
+    static bool done[kMaxDev] = {false};
+    static std::mutex mtx;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mtx);
+    if (!done[dev]) {
+        e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((2 * 4096 + 4096) * sizeof(double2)));
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
 static cudaError_t fft_axis(double2* data, double2* scratch, int L, long es, long s_in, int n_in, long s_out,
                             int n_out, long V, cudaStream_t s)
 {
@@ -223,8 +254,8 @@ static cudaError_t fft_axis(double2* data, double2* scratch, int L, long es, lon
     const LineGeom g{L, es, s_in, s_out, n_in};
     if (L <= 4096 && make_plan(L, plan)) {
         const int B = L >= 2048 ? 1 : (2048 / L < 16 ? 2048 / L : 16);
-        const size_t smem = 2ull * B * L * sizeof(double2);
-        cudaError_t e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t smem = (2ull * B * L + L) * sizeof(double2);
+        cudaError_t e = fft_smem_optin();
         if (e != cudaSuccess) return e;
         const dim3 grid((n_in + B - 1) / B, n_out);
         k_fft_lines<<<grid, 256, smem, s>>>(data, plan, g, B);

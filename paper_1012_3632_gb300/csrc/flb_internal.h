@@ -20,7 +20,9 @@ struct HostModel {
     double om_s, om_b, om_g, kT;
     int nonideal;
     double A, B, rho_c, kappa;
-    int total;  // psi is the total bulk free energy: mu carries -cs^2 ln rho
+    int total;  // psi is the total bulk free energy: F gains cs^2 grad rho
+    int model;  // 0 force-based, 1 modified equilibrium (D2Q9)
+    const double2* swift_xi = nullptr;  // modified equilibrium: FFT of the coloured e/eps noise
     uint64_t seed;
     uint32_t replica;
     int noise_local;
@@ -74,6 +76,17 @@ int set_error(int code, const std::string& msg);
 cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s);
 // In-place forward DFT of n consecutive rows of length X (scratch: X n elements).
 cudaError_t fft_rows(double2* data, int X, int n, double2* scratch, cudaStream_t s);
+
+// Modified-equilibrium model (flb_swift.cu).  swift_table fills chol with
+// (c11, c21, c22) per wavevector, the lower Cholesky factor of the lattice
+// covariance of the e and eps noise; false (with a message) where it is not
+// positive definite.  swift_noise draws the white e/eps normals of `step`,
+// transforms them to Fourier space, colours them with chol and leaves in
+// `out` a field whose real part times 1/V is xi_e and minus imaginary part
+// times 1/V is xi_eps; `work` is scratch (both V complex doubles).
+bool swift_table(const HostModel& m, double* chol, std::string& err);
+cudaError_t swift_noise(const HostModel& m, uint64_t step, const double* chol, double2* work, double2* out,
+                        cudaStream_t s);
 
 // Interface heights of a stripe (flb_capillary.cu): drho is the density
 // deviation field (real_size 4 or 8 bytes), h receives 2 X doubles.

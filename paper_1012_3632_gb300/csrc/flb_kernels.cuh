@@ -239,6 +239,64 @@ __global__ void __launch_bounds__(TX* TY* TZ)
 }
 
 // ---------------------------------------------------------------------------
+// Modified-equilibrium model (Sec. IV.C), D2Q9: the pressure
+// p = p0(rho) - kappa rho lap rho and the square-gradient stress enter the
+// equilibrium (D2Q9::collide_swift); no force.  The density deviation comes
+// from the gather kernel (tile + 1 halo in shared memory), the coloured e/eps
+// noise from swift_noise: xi_e = Re(xi[s]) / V, xi_eps = -Im(xi[s]) / V.
+// p0 = rho psi' - psi (+ rho cs^2 when psi is the excess free energy, pgrad = 0).
+// ---------------------------------------------------------------------------
+template <class R, class S, int TX, int TY>
+__global__ void __launch_bounds__(TX* TY)
+    k_step_swift(const StepArgs<R> a, const __grid_constant__ Planes<S> P, const R* __restrict__ drho,
+                 const double2* __restrict__ xi)
+{
+    using L = D2Q9;
+    constexpr int RX = TX + 2, RY = TY + 2;
+    __shared__ R srho[RY * RX];
+    const int X = a.X, Y = a.Y;
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int x0 = blockIdx.x * TX - 1, y0 = blockIdx.y * TY - 1;
+    for (int e = tid; e < RX * RY; e += TX * TY)
+        srho[e] = drho[wrap_any(x0 + e % RX, X) + (long)X * wrap_any(y0 + e / RX, Y)];
+    __syncthreads();
+    const int x = blockIdx.x * TX + threadIdx.x, y = blockIdx.y * TY + threadIdx.y;
+    if (x >= X || y >= Y) return;
+    const int c = (threadIdx.x + 1) + RX * (threadIdx.y + 1);
+    const R r0 = srho[c];
+    R lap = R(0), gx = R(0), gy = R(0);
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const R v = srho[c + Vel<L>::cx(i) + RX * Vel<L>::cy(i)];
+        lap += R(Vel<L>::w(i)) * (v - r0);
+        if (Vel<L>::cx(i)) gx += R(Vel<L>::cx(i) * Vel<L>::w(i)) * v;
+        if (Vel<L>::cy(i)) gy += R(Vel<L>::cy(i) * Vel<L>::w(i)) * v;
+    }
+    lap *= R(6);
+    gx *= R(3);
+    gy *= R(3);
+    const R rho = a.c.rho0 + r0;
+    const R d = r0 + a.rho0_minus_rhoc;
+    const R psi = d * d * (R(0.5) * a.A + R(0.25) * a.B * d * d);
+    const R psip = d * (a.A + a.B * d * d);
+    const R pex = rho * psip - psi - a.pgrad * rho * R(1.0 / 3.0) - a.kappa * rho * lap;
+    const int s = x + X * y;
+    R xe = R(0), xp = R(0);
+    if (a.c.noise) {
+        const double2 v = xi[s];
+        const double iv = 1.0 / (double)a.V;
+        xe = R(v.x * iv);
+        xp = R(-v.y * iv);
+    }
+    const Nbhd nb(x, y, 0, X, Y, 1);
+    R g[L::Q];
+    pull_planes<L, false>(P, nb, g);
+    L::collide_swift(g, pex, gx, gy, a.kappa, xe, xp, a.c, (uint32_t)s, a.c.step);
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i) store_stream(P.dst[i] + s, g[i]);
+}
+
+// ---------------------------------------------------------------------------
 // Ideal gas, FP32 storage, two sites (x, x+1) per thread with packed FP32
 // arithmetic (F2).  X must be even: a thread's pair then never straddles a row
 // and its populations at (x, x+1) are 8-byte aligned.  Pulls along c_x = 0 are

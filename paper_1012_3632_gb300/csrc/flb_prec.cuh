@@ -408,6 +408,13 @@ struct Prec {
     static cudaError_t step(const HostModel& m, uint64_t t, const void* src, void* dst, const void* drho,
                             cudaStream_t st)
     {
+        if (m.Q == 9 && m.nonideal && m.model == 1) {
+            const StepArgs<R> a = make_args<D2Q9, R>(m, t);
+            const dim3 b(32, 8, 1);
+            k_step_swift<R, S, 32, 8><<<grid_for(m, b), b, 0, st>>>(a, make_planes<S>(src, dst, 9, m.V),
+                                                                      (const R*)drho, m.swift_xi);
+            return cudaGetLastError();
+        }
         if (m.Q == 19) {
             if (m.nonideal) {
                 if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {

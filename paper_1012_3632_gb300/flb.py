@@ -49,7 +49,8 @@ class FLBError(RuntimeError):
 
 class FreeEnergy(ctypes.Structure):
     _fields_ = [("enabled", ctypes.c_int), ("A", ctypes.c_double), ("B", ctypes.c_double),
-                ("rho_c", ctypes.c_double), ("kappa", ctypes.c_double), ("total", ctypes.c_int)]
+                ("rho_c", ctypes.c_double), ("kappa", ctypes.c_double), ("total", ctypes.c_int),
+                ("model", ctypes.c_int)]
 
 
 class InterfaceFit(ctypes.Structure):
@@ -190,11 +191,11 @@ class Context:
         else:
             dims = list(dims) + [1] * (3 - len(dims))
             d = (ctypes.c_int * 3)(*dims)
-            fe = FreeEnergy(0, 0.0, 0.0, 1.0, 0.0, 0)
+            fe = FreeEnergy(0, 0.0, 0.0, 1.0, 0.0, 0, 0)
             if free_energy:
                 fe = FreeEnergy(1, free_energy.get("A", 0.0), free_energy.get("B", 0.0),
                                 free_energy.get("rho_c", 1.0), free_energy.get("kappa", 0.0),
-                                int(bool(free_energy.get("total", False))))
+                                int(bool(free_energy.get("total", False))), int(free_energy.get("model", 0)))
             o = options(**opts)
             h = ctypes.c_void_p()
             _check(L.flb_create(ctypes.byref(h), lattice, d, omega_shear, omega_bulk, omega_ghost, kT,
