@@ -88,6 +88,29 @@ def step_bytes(wl):
 KERNEL_SOURCES = ("flb_device.cuh", "flb_kernels.cuh", "flb_prec.cuh")
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """Max of x over the ranks of the process group (x itself for one rank)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world: int, sites_per_rank: int, steps: int, seconds: float) -> float:
+    """Site updates of all ranks per second, in millions (weak scaling: every
+    rank advances its own lattice of sites_per_rank sites)."""
+    return world * sites_per_rank * steps / seconds / 1e6
+
+
+def replica_word(rank: int) -> int:
+    """Fourth Philox counter word of the replica a rank advances (one per rank)."""
+    return int(rank)
+
+
 def sample_dims(wl):
     """Lattice of the CPU oracle's bounded sample (about 2.6e5 sites)."""
     return (512, 512, 1) if wl["lattice"] == 9 else (64, 64, 64)
@@ -403,7 +426,7 @@ def main():
     dims = wl["dims"]
     V = dims[0] * dims[1] * dims[2]
     ctx = Context(wl["lattice"], dims, om[0], om[1], om[2], kT=wl["kT"], free_energy=wl["fe"], seed=wl["seed"],
-                  precision=wl["precision"], replica=rank, stream=stream.cuda_stream, device=local)
+                  precision=wl["precision"], replica=replica_word(rank), stream=stream.cuda_stream, device=local)
     rho = initial_density(wl, dims)
     u = None if wl["fe"] else inputs.shear_wave(dims, amp=1e-3)
     ctx.init(rho=rho, u=u, thermal=not wl["fe"])
@@ -425,11 +448,8 @@ def main():
     ms = ev0.elapsed_time(ev1)
     kms, kn = ctx.kernel_times()
     ctx.kernel_timing(False)
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * V * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, world)
+    value = whole_job_mlups(world, V, args.steps, ms_max * 1e-3)
 
     # ---- end to end through the C ABI with host buffers ---------------------
     # per run: the initial density field (pinned host -> device) in, K steps,
@@ -448,10 +468,7 @@ def main():
     ctx.moments(RHO, out=host_out)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
-    te = torch.tensor([t_e2e], device="cuda")
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = world * V * args.steps / float(te.item()) / 1e6
+    e2e_value = whole_job_mlups(world, V, args.steps, max_over_ranks(t_e2e, world))
     bytes_u = 0 if wl["fe"] else 3 * V * 8
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (V * 8 + bytes_u) / args.steps,
            "d2h_bytes_per_step": V * 8 / args.steps,
