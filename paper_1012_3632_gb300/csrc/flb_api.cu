@@ -408,7 +408,9 @@ int flb_step(flb_ctx* c, int nsteps)
         if (c->ops->step_needs_density(c->m)) {
             if ((rc = timer_begin(c, 0, &slot))) return rc;
             FLB_CUDA(c->ops->density(c->m, src, c->drho, c->stream));
-            if (c->sw_xi) FLB_CUDA(flb::swift_noise(c->m, c->step, c->sw_chol, c->sw_work, c->sw_xi, c->stream));
+            if (c->sw_xi)
+                FLB_CUDA(flb::swift_noise(c->m, c->step, c->sw_chol, c->sw_work, c->sw_xi, c->prec != FLB_FP64,
+                                          c->stream));
             if ((rc = timer_end(c, slot))) return rc;
         }
         if ((rc = timer_begin(c, 1, &slot))) return rc;

@@ -69,12 +69,22 @@ static bool make_plan(int L, FftPlan& p)
     return n == 1 && p.nrad <= 32;
 }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b)
+// Complex arithmetic on double2 (FP64 transforms) and float2 (FP32 transforms).
+template <class T>
+__device__ __forceinline__ T cmul(T a, T b)
 {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return T{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <class T>
+__device__ __forceinline__ T cadd(T a, T b)
+{
+    return T{a.x + b.x, a.y + b.y};
+}
+template <class T>
+__device__ __forceinline__ T csub(T a, T b)
+{
+    return T{a.x - b.x, a.y - b.y};
+}
 
 // Line geometry: line (i0, i1) starts at i0*s_in + i1*s_out, elements es apart.
 struct LineGeom {
@@ -87,13 +97,14 @@ struct LineGeom {
 // radix R with Ns = product of the radices already applied reads in[j + r L/R],
 // twiddles by exp(-2 pi i r (j mod Ns) / (Ns R)), applies the R-point DFT and
 // writes out[(j / Ns) Ns R + (j mod Ns) + r Ns].  tw[m] = exp(-2 pi i m / L).
-template <int R>
-__device__ __forceinline__ void butterfly(const double2* __restrict__ in, double2* __restrict__ out,
-                                          const double2* __restrict__ tw, int L, int Ns, int j)
+template <int R, class T>
+__device__ __forceinline__ void butterfly(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tw,
+                                          int L, int Ns, int j)
 {
+    using E = decltype(T::x);
     const int stride = L / R;
     const int k = j % Ns;
-    double2 v[R];
+    T v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
     if (Ns > 1) {
@@ -101,29 +112,29 @@ __device__ __forceinline__ void butterfly(const double2* __restrict__ in, double
 #pragma unroll
         for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * step) % L]);
     }
-    double2 y[R];
+    T y[R];
     if constexpr (R == 2) {
         y[0] = cadd(v[0], v[1]);
         y[1] = csub(v[0], v[1]);
     } else if constexpr (R == 4) {
-        const double2 a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
-        const double2 c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        const T a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        const T c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
         y[0] = cadd(a, c);
         y[2] = csub(a, c);
-        y[1] = make_double2(b.x + d.y, b.y - d.x);  // b - i d
-        y[3] = make_double2(b.x - d.y, b.y + d.x);  // b + i d
+        y[1] = T{b.x + d.y, b.y - d.x};  // b - i d
+        y[3] = T{b.x - d.y, b.y + d.x};  // b + i d
     } else if constexpr (R == 3) {
-        const double h = 0.86602540378443864676;  // sqrt(3)/2
-        const double2 t = cadd(v[1], v[2]), u = csub(v[1], v[2]);
+        const E h = E(0.86602540378443864676);  // sqrt(3)/2
+        const T t = cadd(v[1], v[2]), u = csub(v[1], v[2]);
         y[0] = cadd(v[0], t);
-        const double2 m = make_double2(v[0].x - 0.5 * t.x, v[0].y - 0.5 * t.y);
-        y[1] = make_double2(m.x + h * u.y, m.y - h * u.x);  // m - i h u
-        y[2] = make_double2(m.x - h * u.y, m.y + h * u.x);  // m + i h u
+        const T m = T{v[0].x - E(0.5) * t.x, v[0].y - E(0.5) * t.y};
+        y[1] = T{m.x + h * u.y, m.y - h * u.x};  // m - i h u
+        y[2] = T{m.x - h * u.y, m.y + h * u.x};  // m + i h u
     } else {  // R == 5: direct 5-point DFT, exp(-2 pi i m / 5) = tw[m L / 5]
         const int f = L / 5;
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-            double2 acc = v[0];
+            T acc = v[0];
 #pragma unroll
             for (int r = 1; r < 5; ++r) acc = cadd(acc, cmul(v[r], tw[((q * r) % 5) * f]));
             y[q] = acc;
@@ -134,17 +145,20 @@ __device__ __forceinline__ void butterfly(const double2* __restrict__ in, double
     for (int r = 0; r < R; ++r) out[base + r * Ns] = y[r];
 }
 
-__global__ void k_fft_lines(double2* __restrict__ data, const FftPlan plan, const LineGeom g, int B)
+template <class T>
+__global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const LineGeom g, int B)
 {
-    extern __shared__ double2 sm[];
+    using E = decltype(T::x);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T* sm = reinterpret_cast<T*>(smraw);
     const int L = g.L;
-    double2* b0 = sm;
-    double2* b1 = sm + (long)B * L;
-    double2* tw = sm + 2l * B * L;
+    T* b0 = sm;
+    T* b1 = sm + (long)B * L;
+    T* tw = sm + 2l * B * L;
     for (int m = threadIdx.x; m < L; m += blockDim.x) {
         double s, c;
         sincospi(-2.0 * (double)m / (double)L, &s, &c);
-        tw[m] = make_double2(c, s);
+        tw[m] = T{E(c), E(s)};
     }
     const int i0 = blockIdx.x * B;
     const long o1 = (long)blockIdx.y * g.s_out;
@@ -163,8 +177,8 @@ __global__ void k_fft_lines(double2* __restrict__ data, const FftPlan plan, cons
     }
     __syncthreads();
     int Ns = 1;
-    double2* cur = b0;
-    double2* nxt = b1;
+    T* cur = b0;
+    T* nxt = b1;
     for (int p = 0; p < plan.nrad; ++p) {
         const int R = plan.rad[p];
         const int per = L / R;
@@ -179,7 +193,7 @@ __global__ void k_fft_lines(double2* __restrict__ data, const FftPlan plan, cons
         }
         __syncthreads();
         Ns *= R;
-        double2* tmp = cur;
+        T* tmp = cur;
         cur = nxt;
         nxt = tmp;
     }
@@ -196,10 +210,12 @@ __global__ void k_fft_lines(double2* __restrict__ data, const FftPlan plan, cons
     }
 }
 
-// Direct DFT for lengths with prime factors above 5 (small test lattices).
-__global__ void k_dft_lines_naive(const double2* __restrict__ in, double2* __restrict__ out, const LineGeom g,
-                                  int n_out)
+// Direct DFT for lengths with prime factors above 5 (small test lattices),
+// accumulated in double.
+template <class T>
+__global__ void k_dft_lines_naive(const T* __restrict__ in, T* __restrict__ out, const LineGeom g, int n_out)
 {
+    using E = decltype(T::x);
     const long tot = (long)g.n_in * n_out * g.L;
     for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
         const int k = (int)(e % g.L);
@@ -212,9 +228,10 @@ __global__ void k_dft_lines_naive(const double2* __restrict__ in, double2* __res
             const int m = (int)(((long)j * k) % g.L);
             double s, c;
             sincospi(-2.0 * (double)m / (double)g.L, &s, &c);
-            acc = cadd(acc, cmul(in[base + j * g.es], make_double2(c, s)));
+            const T v = in[base + j * g.es];
+            acc = cadd(acc, cmul(make_double2(v.x, v.y), make_double2(c, s)));
         }
-        out[base + k * g.es] = acc;
+        out[base + k * g.es] = T{E(acc.x), E(acc.y)};
     }
 }
 
@@ -227,6 +244,7 @@ bool fft_length_in_place(int L)
 // Opt k_fft_lines into the largest dynamic shared memory it uses (two line
 // buffers of B L <= 8192 elements and a twiddle table of L <= 4096 elements),
 // once per device.
+template <class T>
 static cudaError_t fft_smem_optin()
 {
     constexpr int kMaxDev = 128;
@@ -238,33 +256,34 @@ static cudaError_t fft_smem_optin()
     if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mtx);
     if (!done[dev]) {
-        e = cudaFuncSetAttribute(k_fft_lines, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((2 * 4096 + 4096) * sizeof(double2)));
+        e = cudaFuncSetAttribute(k_fft_lines<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((2 * 4096 + 4096) * sizeof(T)));
         if (e != cudaSuccess) return e;
         done[dev] = true;
     }
     return cudaSuccess;
 }
 
-static cudaError_t fft_axis(double2* data, double2* scratch, int L, long es, long s_in, int n_in, long s_out,
-                            int n_out, long V, cudaStream_t s)
+template <class T>
+static cudaError_t fft_axis(T* data, T* scratch, int L, long es, long s_in, int n_in, long s_out, int n_out, long V,
+                            cudaStream_t s)
 {
     if (L == 1) return cudaSuccess;
     FftPlan plan;
     const LineGeom g{L, es, s_in, s_out, n_in};
     if (L <= 4096 && make_plan(L, plan)) {
         const int B = L >= 2048 ? 1 : (2048 / L < 16 ? 2048 / L : 16);
-        const size_t smem = (2ull * B * L + L) * sizeof(double2);
-        cudaError_t e = fft_smem_optin();
+        const size_t smem = (2ull * B * L + L) * sizeof(T);
+        cudaError_t e = fft_smem_optin<T>();
         if (e != cudaSuccess) return e;
         const dim3 grid((n_in + B - 1) / B, n_out);
-        k_fft_lines<<<grid, 256, smem, s>>>(data, plan, g, B);
+        k_fft_lines<T><<<grid, 256, smem, s>>>(data, plan, g, B);
         return cudaGetLastError();
     }
-    k_dft_lines_naive<<<1024, 256, 0, s>>>(data, scratch, g, n_out);
+    k_dft_lines_naive<T><<<1024, 256, 0, s>>>(data, scratch, g, n_out);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return cudaMemcpyAsync(data, scratch, V * sizeof(double2), cudaMemcpyDeviceToDevice, s);
+    return cudaMemcpyAsync(data, scratch, V * sizeof(T), cudaMemcpyDeviceToDevice, s);
 }
 
 cudaError_t fft_rows(double2* data, int X, int n, double2* scratch, cudaStream_t s)
@@ -272,7 +291,8 @@ cudaError_t fft_rows(double2* data, int X, int n, double2* scratch, cudaStream_t
     return fft_axis(data, scratch, X, 1, X, n, (long)X * n, 1, (long)X * n, s);
 }
 
-cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s)
+template <class T>
+static cudaError_t fft3d_t(T* data, int X, int Y, int Z, T* scratch, cudaStream_t s)
 {
     const long V = (long)X * Y * Z;
     cudaError_t e;
@@ -282,6 +302,16 @@ cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStre
     if ((e = fft_axis(data, scratch, Y, X, 1, X, (long)X * Y, Z, V, s)) != cudaSuccess) return e;
     // z lines: inner x, outer y
     return fft_axis(data, scratch, Z, (long)X * Y, 1, X, X, Y, V, s);
+}
+
+cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s)
+{
+    return fft3d_t(data, X, Y, Z, scratch, s);
+}
+
+cudaError_t fft3d(float2* data, int X, int Y, int Z, float2* scratch, cudaStream_t s)
+{
+    return fft3d_t(data, X, Y, Z, scratch, s);
 }
 
 __global__ void k_power(const double2* __restrict__ d, long V, double* __restrict__ acc, double* __restrict__ out)

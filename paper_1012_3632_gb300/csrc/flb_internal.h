@@ -22,7 +22,7 @@ struct HostModel {
     double A, B, rho_c, kappa;
     int total;  // psi is the total bulk free energy: F gains cs^2 grad rho
     int model;  // 0 force-based, 1 modified equilibrium (D2Q9)
-    const double2* swift_xi = nullptr;  // modified equilibrium: FFT of the coloured e/eps noise
+    const void* swift_xi = nullptr;  // modified equilibrium: FFT of the coloured e/eps noise (double2 or float2)
     uint64_t seed;
     uint32_t replica;
     int noise_local;
@@ -72,8 +72,10 @@ bool fft_length_in_place(int L);
 // Record the calling thread's last error message (flb_last_error) and return code.
 int set_error(int code, const std::string& msg);
 
-// In-place forward DFT along every axis of length > 1 of a complex X*Y*Z field.
+// In-place forward DFT along every axis of length > 1 of a complex X*Y*Z field
+// (FP64, and an FP32 form for fields whose precision needs no more).
 cudaError_t fft3d(double2* data, int X, int Y, int Z, double2* scratch, cudaStream_t s);
+cudaError_t fft3d(float2* data, int X, int Y, int Z, float2* scratch, cudaStream_t s);
 // In-place forward DFT of n consecutive rows of length X (scratch: X n elements).
 cudaError_t fft_rows(double2* data, int X, int n, double2* scratch, cudaStream_t s);
 
@@ -83,9 +85,10 @@ cudaError_t fft_rows(double2* data, int X, int n, double2* scratch, cudaStream_t
 // positive definite.  swift_noise draws the white e/eps normals of `step`,
 // transforms them to Fourier space, colours them with chol and leaves in
 // `out` a field whose real part times 1/V is xi_e and minus imaginary part
-// times 1/V is xi_eps; `work` is scratch (both V complex doubles).
+// times 1/V is xi_eps; `work` is scratch (both V complex numbers, float2 when
+// fp32, else double2).
 bool swift_table(const HostModel& m, double* chol, std::string& err);
-cudaError_t swift_noise(const HostModel& m, uint64_t step, const double* chol, double2* work, double2* out,
+cudaError_t swift_noise(const HostModel& m, uint64_t step, const double* chol, void* work, void* out, bool fp32,
                         cudaStream_t s);
 
 // Interface heights of a stripe (flb_capillary.cu): drho is the density

@@ -15,6 +15,8 @@
 // F = -rho grad mu at each site.
 #pragma once
 
+#include <type_traits>
+
 #include "flb_device.cuh"
 
 namespace flb {
@@ -246,10 +248,13 @@ __global__ void __launch_bounds__(TX* TY* TZ)
 // noise from swift_noise: xi_e = Re(xi[s]) / V, xi_eps = -Im(xi[s]) / V.
 // p0 = rho psi' - psi (+ rho cs^2 when psi is the excess free energy, pgrad = 0).
 // ---------------------------------------------------------------------------
+template <class R>
+using NoiseField = typename std::conditional<std::is_same<R, double>::value, double2, float2>::type;
+
 template <class R, class S, int TX, int TY>
 __global__ void __launch_bounds__(TX* TY)
     k_step_swift(const StepArgs<R> a, const __grid_constant__ Planes<S> P, const R* __restrict__ drho,
-                 const double2* __restrict__ xi)
+                 const NoiseField<R>* __restrict__ xi)
 {
     using L = D2Q9;
     constexpr int RX = TX + 2, RY = TY + 2;
@@ -283,7 +288,7 @@ __global__ void __launch_bounds__(TX* TY)
     const int s = x + X * y;
     R xe = R(0), xp = R(0);
     if (a.c.noise) {
-        const double2 v = xi[s];
+        const NoiseField<R> v = xi[s];
         const double iv = 1.0 / (double)a.V;
         xe = R(v.x * iv);
         xp = R(-v.y * iv);

@@ -412,7 +412,8 @@ struct Prec {
             const StepArgs<R> a = make_args<D2Q9, R>(m, t);
             const dim3 b(32, 8, 1);
             k_step_swift<R, S, 32, 8><<<grid_for(m, b), b, 0, st>>>(a, make_planes<S>(src, dst, 9, m.V),
-                                                                      (const R*)drho, m.swift_xi);
+                                                                      (const R*)drho,
+                                                                      (const NoiseField<R>*)m.swift_xi);
             return cudaGetLastError();
         }
         if (m.Q == 19) {

@@ -19,7 +19,9 @@
 // collision's own Philox draw for the modes e and eps), Z = FFT(z_e + i z_eps),
 // per k the pair (E, P) = ((Z(k) + Z*(-k))/2, (Z(k) - Z*(-k))/(2i)) is
 // multiplied by the lower Cholesky factor of C(k), and an FFT of the conjugate
-// gives V times the conjugate of the inverse transform.
+// gives V times the conjugate of the inverse transform.  FP64 storage
+// colours the noise with FP64 transforms, FP32 and BF16 storage with FP32
+// transforms (a random field that needs no more precision).
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -33,35 +35,53 @@ namespace flb {
 namespace {
 
 // Z(r) = z_e(r) + i z_eps(r): normals 0 and 5 of the D2Q9 collision draw
-// (calls 0 and 1 of tag 0), in FP64.
-__global__ void k_swift_white(PhiloxKeys key, uint32_t step, uint32_t replica, long V, double2* __restrict__ Z)
+// (calls 0 and 1 of tag 0), in FP64, stored as T (double2 or float2).
+template <class T>
+__global__ void k_swift_white(PhiloxKeys key, uint32_t step, uint32_t replica, long V, T* __restrict__ Z)
 {
+    using E = decltype(T::x);
     for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < V; s += (long)gridDim.x * blockDim.x) {
         double a[4], b[4];
         normals4<double>(key, (uint32_t)s, step, 0u, replica, a);
         normals4<double>(key, (uint32_t)s, step, 1u, replica, b);
-        Z[s] = make_double2(a[0], b[1]);
+        Z[s] = T{E(a[0]), E(b[1])};
     }
 }
 
 // out(k) = conj(Ze'(k) + i Zp'(k)) with (Ze', Zp') = chol(k) (E, P).
-__global__ void k_swift_colour(const double2* __restrict__ Z, const double* __restrict__ chol, int X, int Y,
-                               double2* __restrict__ out)
+template <class T>
+__global__ void k_swift_colour(const T* __restrict__ Z, const double* __restrict__ chol, int X, int Y,
+                               T* __restrict__ out)
 {
+    using E = decltype(T::x);
     const long V = (long)X * Y;
     for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < V; s += (long)gridDim.x * blockDim.x) {
         const int nx = (int)(s % X), ny = (int)(s / X);
         const long sm = (long)((X - nx) % X) + (long)X * ((Y - ny) % Y);  // -k
-        const double2 zk = Z[s], zm = Z[sm];
+        const T zk = Z[s], zm = Z[sm];
         // E = (Z(k) + conj Z(-k)) / 2, P = (Z(k) - conj Z(-k)) / (2i)
-        const double er = 0.5 * (zk.x + zm.x), ei = 0.5 * (zk.y - zm.y);
-        const double pr = 0.5 * (zk.y + zm.y), pi = -0.5 * (zk.x - zm.x);
-        const double c11 = chol[3 * s], c21 = chol[3 * s + 1], c22 = chol[3 * s + 2];
-        const double Er = c11 * er, Ei = c11 * ei;
-        const double Pr = c21 * er + c22 * pr, Pi = c21 * ei + c22 * pi;
+        const E er = E(0.5) * (zk.x + zm.x), ei = E(0.5) * (zk.y - zm.y);
+        const E pr = E(0.5) * (zk.y + zm.y), pi = E(-0.5) * (zk.x - zm.x);
+        const E c11 = E(chol[3 * s]), c21 = E(chol[3 * s + 1]), c22 = E(chol[3 * s + 2]);
+        const E Er = c11 * er, Ei = c11 * ei;
+        const E Pr = c21 * er + c22 * pr, Pi = c21 * ei + c22 * pi;
         // E' + i P' = (Er - Pi) + i (Ei + Pr); conjugate
-        out[s] = make_double2(Er - Pi, -(Ei + Pr));
+        out[s] = T{Er - Pi, -(Ei + Pr)};
     }
+}
+
+template <class T>
+cudaError_t swift_noise_t(const HostModel& m, uint64_t step, const double* chol, T* work, T* out, cudaStream_t s)
+{
+    const long V = m.V;
+    const unsigned nb = (unsigned)std::min<long>((V + 255) / 256, 152 * 16);
+    k_swift_white<T><<<nb, 256, 0, s>>>(philox_keys(m.seed), (uint32_t)step, m.replica, V, work);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = fft3d(work, m.X, m.Y, 1, out, s)) != cudaSuccess) return e;
+    k_swift_colour<T><<<nb, 256, 0, s>>>(work, chol, m.X, m.Y, out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return fft3d(out, m.X, m.Y, 1, work, s);
 }
 
 }  // namespace
@@ -102,18 +122,11 @@ bool swift_table(const HostModel& m, double* chol, std::string& err)
     return true;
 }
 
-cudaError_t swift_noise(const HostModel& m, uint64_t step, const double* chol, double2* work, double2* out,
+cudaError_t swift_noise(const HostModel& m, uint64_t step, const double* chol, void* work, void* out, bool fp32,
                         cudaStream_t s)
 {
-    const long V = m.V;
-    const unsigned nb = (unsigned)std::min<long>((V + 255) / 256, 152 * 16);
-    k_swift_white<<<nb, 256, 0, s>>>(philox_keys(m.seed), (uint32_t)step, m.replica, V, work);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    if ((e = fft3d(work, m.X, m.Y, 1, out, s)) != cudaSuccess) return e;
-    k_swift_colour<<<nb, 256, 0, s>>>(work, chol, m.X, m.Y, out);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return fft3d(out, m.X, m.Y, 1, work, s);
+    if (fp32) return swift_noise_t(m, step, chol, (float2*)work, (float2*)out, s);
+    return swift_noise_t(m, step, chol, (double2*)work, (double2*)out, s);
 }
 
 }  // namespace flb
