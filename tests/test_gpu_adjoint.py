@@ -69,7 +69,7 @@ def _loss_of(g0_dev, theta, cfg):
         return density_spectrum_loss(run(g0_dev, theta, cfg), cfg["dims"]).item()
 
 
-def test_config4_gradients_match_finite_differences():
+def test_64cubed_200_steps_gradients_match_finite_differences():
     dims = (64, 64, 64)
     cfg = dict(dims=dims, kT=1e-6, seed=5, precision="fp64", nsteps=200, every=20, nonideal=True,
                rho_c=FE["rho_c"])

@@ -34,7 +34,7 @@ def _run_both(Q, dims, prec, steps, fe=None, rho=None, u=None, thermal=False, **
     return got, want
 
 
-def test_config0_d2q9_fp64_100_steps():
+def test_d2q9_32x32_fp64_ideal_100_steps():
     """D2Q9 ideal gas 32x32, FP64, rho0 = 1, kT = 1e-4, all rates 1, f = w rho0, seed 1."""
     got, want = _run_both(9, (32, 32, 1), "fp64", 100, kT=1e-4, omega_shear=1.0, omega_bulk=1.0,
                           omega_ghost=1.0, seed=1)
@@ -77,7 +77,7 @@ def test_fp64_random_state_noise_rho0():
 
 
 @pytest.mark.parametrize("dims", [(16, 16, 16), (17, 9, 8), (2, 5, 3)])
-def test_fp32_config1_like_100_steps(dims):
+def test_fp32_d3q19_ideal_shear_wave_100_steps(dims):
     """D3Q19 ideal, FP32 deviations, kT = 1e-5, rates (1.2, 1, 1), shear wave + thermal start.
     Even X runs the packed two-site kernel, odd X the one-site kernel."""
     u = inputs.shear_wave(dims, amp=1e-3)
@@ -87,7 +87,7 @@ def test_fp32_config1_like_100_steps(dims):
 
 
 @pytest.mark.parametrize("dims", [(16, 14, 12), (15, 12, 10), (2, 3, 4), (34, 6, 5), (72, 10, 6), (4, 5, 3)])
-def test_fp32_config2_like_100_steps(dims):
+def test_fp32_d3q19_nonideal_100_steps(dims):
     """D3Q19 non-ideal (A=-0.01, B=0.1, rho_c=1, kappa=0.02), FP32, kT = 1e-6, rates 1.
     Even X runs the packed two-site kernel, odd X the one-site kernel."""
     rho = inputs.uniform_density(dims, seed=3)
@@ -272,7 +272,7 @@ def _window_check(Q, dims, prec, steps, fe, rho, u, thermal, kw, centres, tol):
         assert np.abs(f[:, s_glob] - fw[:, s_loc]).max() <= tol, cen
 
 
-def test_full_size_config2_sampled():
+def test_full_size_nonideal_256cubed_sampled():
     """256^3 non-ideal FP32 (the benchmark workload): 3 steps, 4 sampled sites."""
     dims = (256, 256, 256)
     rho = inputs.uniform_density(dims, seed=3)
@@ -281,7 +281,7 @@ def test_full_size_config2_sampled():
     _window_check(19, dims, "fp32", 3, FE, rho, None, False, kw, centres, TOL["fp32"])
 
 
-def test_full_size_config1_sampled():
+def test_full_size_ideal_128cubed_sampled():
     """128^3 ideal FP32 with shear wave and thermal start: 5 steps, 4 sampled sites."""
     dims = (128, 128, 128)
     u = inputs.shear_wave(dims, amp=1e-3)

@@ -31,7 +31,7 @@ def _kgrid(dims):
 
 
 @pytest.fixture(scope="module")
-def config1_run():
+def ideal128_run():
     """128^3 D3Q19 ideal gas, FP32, kT = 1e-5, rates (1.2, 1.0, 1.0), shear wave
     u_x = 1e-3 sin(2 pi z / 128) plus thermal start, 10^4 steps; snapshots
     every 100 steps."""
@@ -55,8 +55,8 @@ def config1_run():
     return dict(dims=dims, kT=kT, om=om, var=var, Sjx=Sjx, amps=np.array(amps), times=np.array(times))
 
 
-def test_mode_temperatures_within_one_percent(config1_run):
-    r = config1_run
+def test_mode_temperatures_within_one_percent(ideal128_run):
+    r = ideal128_run
     V = np.prod(r["dims"])
     T = CS2 * r["var"] / N19 / r["kT"]
     # j_x carries the deterministic wave: take its variance from the spectrum
@@ -70,8 +70,8 @@ def test_mode_temperatures_within_one_percent(config1_run):
     assert np.all(np.abs(T - 1.0) < 0.01), T
 
 
-def test_shear_wave_decay_rate(config1_run):
-    r = config1_run
+def test_shear_wave_decay_rate(ideal128_run):
+    r = ideal128_run
     k = 2 * np.pi / r["dims"][2]
     nu = CS2 * (1.0 / r["om"] - 0.5)
     # the thermal fluctuation of the same Fourier mode (~3e-6, correlated over
