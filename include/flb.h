@@ -118,7 +118,8 @@ typedef struct {
                    the square-gradient stress kappa (d_a rho d_b rho - |grad rho|^2
                    delta_ab / 2) in p_ww and p_xy, with p0 = rho psi' - psi
                    (+ rho cs^2 when total = 0); the e and eps noise is drawn in
-                   Fourier space with the k-dependent covariance of Eq. (noise-yeo)
+                   Fourier space around rho0 (times sqrt(rho / rho0) per site with
+                   noise_rho_local) with the k-dependent covariance of Eq. (noise-yeo)
                    (corner 6 (c_s^2(k) - cs^2)(lambda_e + lambda_eps), from the FDT)
                    mapped to the lattice as in Sec. V, c_s^2(k) = dp0/drho(rho0) +
                    kappa rho0 K2(k) with K2 the symbol of -lap; flb_create fails

@@ -417,9 +417,13 @@ static void collide(const orc_params* p, const orc_lattice* L, const double f[],
             /* Eq. (noise-lbe): variance rho kT (2-omega) omega N_a / s2, Delta V = 1 */
             double var = rho_n * p->kT * (2.0 - om) * om * L->N[a] / S2;
             xi = sqrt(var) * z[k];
-            /* modified equilibrium: e and eps carry the k-dependent noise */
-            if (sw && a == 3) xi = sw[3];
-            if (sw && a == 8) xi = sw[4];
+            /* modified equilibrium: e and eps carry the k-dependent noise, built
+             * around rho0 and scaled by sqrt(rho / rho0) for the local density
+             * (Sec. VI: local values in inhomogeneous states) */
+            if (sw && (a == 3 || a == 8)) {
+                double sc = p->noise_rho_local ? sqrt(rho / p->rho0) : 1.0;
+                xi = sc * (a == 3 ? sw[3] : sw[4]);
+            }
             k++;
         }
         ms[a] = m[a] - om * (m[a] - meq[a]) + (1.0 - 0.5 * om) * mF[a] + xi;

@@ -362,8 +362,10 @@ struct D2Q9 {
             noise_normals<2>(P.key, site, step, P.replica, z);
 #pragma unroll
             for (int k = 1; k < 5; ++k) Dm[3 + k] += P.ns[k] * (sr * z[k]);
-            Dm[3] += xe * R(1.0 / 4.0);   // / N_e
-            Dm[8] += xp * R(1.0 / 16.0);  // / N_eps
+            // the coloured noise is built around rho0: sqrt(rho / rho0) for the local density
+            const R sc = sr * rcp_(R(P.sqrt_rho0));
+            Dm[3] += (sc * xe) * R(1.0 / 4.0);   // / N_e
+            Dm[8] += (sc * xp) * R(1.0 / 16.0);  // / N_eps
         }
         add_back(Dm, g);
     }

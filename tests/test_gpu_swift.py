@@ -103,3 +103,19 @@ def test_swift_arguments_are_checked():
     # kappa large enough that 2 - 3 c_s^2(k) < 0 at the largest k: no covariance
     with pytest.raises(FLBError):
         Context(9, (8, 8, 1), 1.0, kT=1e-6, free_energy=dict(_fe(), kappa=0.5))
+
+
+def test_swift_capillary_spectrum_matches_capillary_theory():
+    """Fluctuating D2Q9 stripe (256 x 128, thickness 64) of the modified-equilibrium
+    Landau fluid, tau = 1, kT = 1e-7: the height spectrum averaged over
+    0 < k <= 0.6 equals kT / (sigma (2 - 2 cos k)) of Eq. (capill-static) with
+    the mean-field sigma of Eq. (surf-tension) within 15 % (Sec. VI: the
+    modified-equilibrium model reproduces the capillary spectrum)."""
+    from paper_1012_3632_gb300.capillary import run_stripe
+
+    k, S, n, _ = run_stripe(steps=200000, snapshots=800, X=256, Y=128, thickness=64, kT=1e-7, model=1)
+    assert n == 800
+    sig = cap.surface_tension(RL, RV, BETA, KAPPA)
+    m = (k > 0) & (k <= 0.6)
+    ratio = (S[m] / cap.capillary_spectrum(k[m], 1e-7, sig)).mean()
+    assert abs(ratio - 1) < 0.15, ratio
