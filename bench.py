@@ -55,6 +55,13 @@ WORKLOADS = {
                               name="D2Q9 liquid stripe 1024x400 (thickness 200) of the Landau double well "
                                    "beta (rho-0.5)^2 (rho-1)^2, beta=0.1, kappa=0.08, as total bulk free energy "
                                    "(F = -rho grad mu + cs^2 grad rho), kT=1e-7, tau=1, FP32 deviations"),
+    "swift1024x400": dict(lattice=9, dims=(1024, 400, 1), precision="fp32",
+                          fe=dict(A=-0.025, B=0.4, rho_c=0.75, kappa=0.08, total=True, model=1), kT=1e-7,
+                          omega=(1.0, 1.0, 1.0), seed=11, stripe=200,
+                          name="D2Q9 liquid stripe 1024x400 (thickness 200) of the Landau double well "
+                               "beta (rho-0.5)^2 (rho-1)^2, beta=0.1, kappa=0.08, modified-equilibrium model "
+                               "(pressure in the equilibrium, e/eps noise coloured by FFT), kT=1e-7, tau=1, "
+                               "FP32 deviations"),
     "ideal128": dict(lattice=19, dims=(128, 128, 128), precision="fp32", fe=None, kT=1e-5,
                      omega=(1.2, 1.0, 1.0), seed=2,
                      name="D3Q19 ideal gas, 128^3 periodic, FP32 deviations, kT=1e-5, "
@@ -81,6 +88,9 @@ def step_bytes(wl):
     rb = 8 if wl["precision"] == "fp64" else 4
     if not wl["fe"]:
         return 2 * Q * e, 0, 2 * Q * e
+    if wl["fe"].get("model", 0) == 1:  # + the density and the coloured e/eps noise field
+        nf = 16 if wl["precision"] == "fp64" else 8
+        return 2 * Q * e + rb + nf, Q * e + rb, 2 * Q * e + rb + nf
     if Q == 9:
         return 2 * Q * e + rb, Q * e + rb, 2 * Q * e + rb
     return 3 * Q * e + 2 * rb, 0, 2 * Q * e
@@ -138,6 +148,8 @@ def initial_density(wl, dims):
 def kernel_name(wl):
     """The step kernel the library launches for this workload."""
     packed = wl["precision"] == "fp32" and wl["dims"][0] % 2 == 0 and wl["lattice"] == 19
+    if wl["fe"] and wl["fe"].get("model", 0) == 1:
+        return "k_step_swift"
     if wl["fe"] and wl["lattice"] == 19:
         return "k_step_march2" if packed else "k_step_march"
     return "k_step2" if packed else "k_step"
