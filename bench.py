@@ -122,9 +122,17 @@ def replica_word(rank: int) -> int:
     return int(rank)
 
 
-def sample_dims(wl):
-    """Lattice of the CPU oracle's bounded sample (about 2.6e5 sites)."""
-    return (512, 512, 1) if wl["lattice"] == 9 else (64, 64, 64)
+def sample_dims(wl, sites=262144):
+    """Lattice of the CPU oracle's bounded sample, about `sites` sites (the
+    modified-equilibrium oracle colours its noise with a direct DFT, so its
+    sample is kept small)."""
+    if wl["fe"] and wl["fe"].get("model", 0) == 1:
+        sites = min(sites, 16384)
+    if wl["lattice"] == 9:
+        n = max(8, 2 * int(round(sites ** 0.5 / 2)))
+        return (n, n, 1)
+    n = max(8, 2 * int(round(sites ** (1 / 3) / 2)))
+    return (n, n, n)
 
 
 def initial_density(wl, dims):
@@ -357,6 +365,9 @@ def adjoint_vs_plain(dims=(64, 64, 64), nsteps=200, every=20, precision="fp32"):
             "backward_over_plain": t_bwd / t_plain, "grad_theta": [float(v) for v in theta.grad]}
 
 
+REF_BUDGET_S = 120.0  # wall-clock budget of the reference arm's warm-up + timed steps
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return
@@ -365,13 +376,25 @@ def run_reference(args, wl, rank):
     import oracle
     from paper_1012_3632_gb300 import inputs
 
-    dims = sample_dims(wl)
     om = wl["omega"]
     fe = wl["fe"] or {}
-    p = oracle.Params(Q=wl["lattice"], dims=dims, omega_shear=om[0], omega_bulk=om[1], omega_ghost=om[2],
-                      kT=wl["kT"], nonideal=bool(wl["fe"]), seed=wl["seed"], **fe)
-    rho = initial_density(wl, dims)
-    f = oracle.init(p, rho=rho, thermal=not wl["fe"])
+
+    def setup(dims):
+        p = oracle.Params(Q=wl["lattice"], dims=dims, omega_shear=om[0], omega_bulk=om[1], omega_ghost=om[2],
+                          kT=wl["kT"], nonideal=bool(wl["fe"]), seed=wl["seed"], **fe)
+        return p, oracle.init(p, rho=initial_density(wl, dims), thermal=not wl["fe"])
+
+    # size the per-step sample so that warm-up and timed steps take about
+    # REF_BUDGET_S in total: time two steps of a small probe lattice first
+    pdims = sample_dims(wl, 4096)
+    p, f = setup(pdims)
+    t0 = time.perf_counter()
+    for t in range(2):
+        f = oracle.step(p, f, t)
+    per_site = (time.perf_counter() - t0) / (2 * np.prod(pdims))
+    sites = REF_BUDGET_S / max(per_site, 1e-9) / (args.steps + args.warmup)
+    dims = sample_dims(wl, int(min(262144, max(4096, sites))))
+    p, f = setup(dims)
     for t in range(args.warmup):
         f = oracle.step(p, f, t)
     t0 = time.perf_counter()
