@@ -308,8 +308,8 @@ __global__ void __launch_bounds__(TX* TY)
 // single 8-byte loads; along c_x = +-1 the pair comes from (x-1, x) or
 // (x+1, x+2).  Block = TXT x TY x TZ threads covering 2 TXT x TY x TZ sites.
 // ---------------------------------------------------------------------------
-template <class L, int TXT, int TY, int TZ>
-__global__ void __launch_bounds__(TXT* TY* TZ)
+template <class L, int TXT, int TY, int TZ, int MINB = 1>
+__global__ void __launch_bounds__(TXT* TY* TZ, MINB)
     k_step2(const StepArgs<float> a, const __grid_constant__ Planes<float> P)
 {
     const int x = 2 * (blockIdx.x * TXT + threadIdx.x);

@@ -22,6 +22,18 @@
 #ifndef FLB_PACKED
 #define FLB_PACKED 1
 #endif
+#ifndef FLB_STEP2_TXT
+#define FLB_STEP2_TXT 32
+#endif
+#ifndef FLB_STEP2_TY
+#define FLB_STEP2_TY 2
+#endif
+#ifndef FLB_STEP2_TZ
+#define FLB_STEP2_TZ 2
+#endif
+#ifndef FLB_STEP2_MINB
+#define FLB_STEP2_MINB 4
+#endif
 #ifndef FLB_MARCH2_MINB
 #define FLB_MARCH2_MINB 3
 #endif
@@ -444,11 +456,12 @@ struct Prec {
             }
             if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
                 if (m.X % 2 == 0 && FLB_PACKED) {
-                    constexpr int TXT = 16, TY = 4, TZ = 2;
+                    constexpr int TXT = FLB_STEP2_TXT, TY = FLB_STEP2_TY, TZ = FLB_STEP2_TZ;
                     const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                     const dim3 b(TXT, TY, TZ);
                     const dim3 g((m.X / 2 + TXT - 1) / TXT, (m.Y + TY - 1) / TY, (m.Z + TZ - 1) / TZ);
-                    k_step2<D3Q19, TXT, TY, TZ><<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
+                    k_step2<D3Q19, TXT, TY, TZ, FLB_STEP2_MINB>
+                        <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                     return cudaGetLastError();
                 }
             }
