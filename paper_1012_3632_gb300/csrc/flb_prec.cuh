@@ -361,6 +361,50 @@ __global__ void k_cons_partials(const S* __restrict__ src, double* __restrict__ 
     block_sum_row<4>(v, partials + block_linear() * 4);
 }
 
+// Single-precision state: the same sums without FP64 arithmetic per population
+// (the FP64 rate of the part is a small fraction of its FP32 rate).  Each
+// thread walks the sites with a fixed stride and adds every population into
+// (hi, lo) single-precision pairs by Knuth's TwoSum, so the rounding error of
+// each addition is kept in lo; the pairs become doubles only for the block sum.
+// The grid depends on V alone, so the result is deterministic.
+constexpr int kConsThreads = 256, kConsBlocksMax = 152 * 8;
+
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float b)
+{
+    const float s = hi + b;
+    const float bb = s - hi;
+    lo += (hi - (s - bb)) + (b - bb);
+    hi = s;
+}
+
+template <class L, class S>
+__global__ void __launch_bounds__(kConsThreads) k_cons_partials_sp(const S* __restrict__ src,
+                                                                   double* __restrict__ partials, long V)
+{
+    float hi[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
+    for (long s = blockIdx.x * (long)kConsThreads + threadIdx.x; s < V; s += (long)gridDim.x * kConsThreads) {
+        float g[L::Q];
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) g[i] = load_s<float>(src + (long)i * V + s);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            two_sum_add(hi[0], lo[0], g[i]);
+            if (Vel<L>::cx(i) != 0) two_sum_add(hi[1], lo[1], Vel<L>::cx(i) > 0 ? g[i] : -g[i]);
+            if (Vel<L>::cy(i) != 0) two_sum_add(hi[2], lo[2], Vel<L>::cy(i) > 0 ? g[i] : -g[i]);
+            if (Vel<L>::cz(i) != 0) two_sum_add(hi[3], lo[3], Vel<L>::cz(i) > 0 ? g[i] : -g[i]);
+        }
+    }
+    double v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (double)hi[k] + (double)lo[k];
+    block_sum_row<4>(v, partials + (long)blockIdx.x * 4);
+}
+
+inline int cons_blocks(long V)
+{
+    return (int)std::min<long>((V + kConsThreads - 1) / kConsThreads, kConsBlocksMax);
+}
+
 template <class L, class R, class S>
 __global__ void k_mode_field(const S* __restrict__ src, int mode, double2* __restrict__ out, int X, int Y, int Z)
 {
@@ -566,6 +610,15 @@ struct Prec {
     static cudaError_t cons_partials(const HostModel& m, const void* src, double* partials, int* nrows,
                                      cudaStream_t st)
     {
+        if constexpr (std::is_same<R, float>::value) {
+            // at most rows(m): cons_blocks(V) <= ceil(V / 256) <= the site grid
+            *nrows = cons_blocks(m.V);
+            if (m.Q == 19)
+                k_cons_partials_sp<D3Q19, S><<<*nrows, kConsThreads, 0, st>>>((const S*)src, partials, m.V);
+            else
+                k_cons_partials_sp<D2Q9, S><<<*nrows, kConsThreads, 0, st>>>((const S*)src, partials, m.V);
+            return cudaGetLastError();
+        }
         *nrows = rows(m);
         if (m.Q == 19) {
             const dim3 b = site_block<D3Q19>();

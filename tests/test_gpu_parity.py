@@ -288,3 +288,22 @@ def test_full_size_ideal_128cubed_sampled():
     kw = dict(kT=1e-5, omega_shear=1.2, omega_bulk=1.0, omega_ghost=1.0, seed=2)
     centres = [(0, 0, 0), (127, 64, 1), (5, 127, 127), (90, 33, 64)]
     _window_check(19, dims, "fp32", 5, None, None, u, True, kw, centres, TOL["fp32"])
+
+
+@pytest.mark.parametrize("Q,dims,prec", [
+    (19, (72, 70, 64), "fp32"), (19, (72, 70, 64), "bf16"), (9, (613, 517, 1), "fp32"), (19, (5, 3, 2), "fp32"),
+])
+def test_conservation_sums_are_exact_sums_of_the_state(Q, dims, prec):
+    """flb_conservation on single-precision state (compensated single-precision
+    sums, several sites per thread, a ragged last block) equals the FP64 sum of
+    the populations: mass and momentum, the invariants of the collision (Sec. II)."""
+    rho = inputs.uniform_density(dims, seed=5)
+    with Context(Q, dims, 1.2, kT=1e-5, seed=6, precision=prec) as ctx:
+        ctx.init(rho=rho, thermal=True)
+        ctx.step(3)
+        f = ctx.get_populations()
+        cons = ctx.conservation()
+    c = oracle.lattice(Q).c.astype(float)
+    V = int(np.prod(dims))
+    assert abs(cons[0] - f.sum()) <= 1e-13 * V
+    assert np.abs(np.asarray(cons[1:]) - (c.T @ f).sum(axis=1)).max() <= 1e-13 * V
