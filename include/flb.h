@@ -75,6 +75,7 @@ extern "C" {
 #define FLB_EDIVERGED (-4) /* non-finite mass or momentum detected after a step */
 #define FLB_ETIMEOUT (-5)  /* reserved: a bounded device-side wait gave up */
 #define FLB_EIO (-6)       /* checkpoint file could not be read or written */
+#define FLB_EBOUNDS (-7)   /* a guard zone around a device buffer was overwritten */
 
 typedef struct flb_ctx flb_ctx;
 
@@ -136,6 +137,10 @@ typedef struct {
     int device;          /* CUDA device ordinal; -1 (default): the current device */
     int check_every;     /* flb_step checks mass/momentum for NaN/Inf every this many
                             steps (0: never; default 0) */
+    int guard;           /* 1: the two population buffers and the density field get
+                            64 KiB guard zones of a fixed byte pattern on both sides,
+                            checked by flb_check_guards (a bounds check of the
+                            kernels' writes for debugging; default 0) */
 } flb_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -224,6 +229,14 @@ int flb_interface_heights(flb_ctx* ctx, const flb_interface_fit* fit, double* h)
  * first call. */
 int flb_height_spectrum(flb_ctx* ctx, const flb_interface_fit* fit, double* S, int accumulate);
 
+/* Bounds check of the kernels' writes (contexts created with opt.guard = 1):
+ * waits for the context's stream, copies every guard zone to the host and
+ * returns FLB_OK when each still holds its pattern, FLB_EBOUNDS when one was
+ * overwritten (flb_last_error names the buffer, the side and the first changed
+ * byte), FLB_EINVAL when the context has no guard zones.  Reads outside a
+ * buffer are not detected. */
+int flb_check_guards(flb_ctx* ctx);
+
 /* Total mass and momentum of the current state, summed on the GPU in double:
  * out[0] = sum rho, out[1..3] = sum_r sum_i f_i c_i (z component 0 for D2Q9). */
 int flb_conservation(flb_ctx* ctx, double out[4]);
@@ -231,6 +244,14 @@ int flb_conservation(flb_ctx* ctx, double out[4]);
 /* Read / write the pre-collision populations f^LB (host, Q*V doubles). */
 int flb_get_populations(flb_ctx* ctx, double* f);
 int flb_set_populations(flb_ctx* ctx, const double* f);
+
+/* Pre-collision populations f^LB at n chosen sites, without copying the
+ * lattice (sampling large lattices).  sites: host, n site indices
+ * x + X*(y + Y*z), each in [0, V) (else FLB_EINVAL before any GPU work; n = 0
+ * does nothing).  f: host, Q*n doubles, f[i*n + k] = f_i at sites[k], the same
+ * values as flb_get_populations' f[i*V + sites[k]].  Device memory for the
+ * list and the result is allocated and freed inside the call. */
+int flb_get_sites(flb_ctx* ctx, const long long* sites, int n, double* f);
 
 /* ---- Adjoint -----------------------------------------------------------------
  * Device-side state exchange and the adjoint (reverse-mode derivative) of one

@@ -66,6 +66,15 @@ struct flb_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     int check_every = 0;
+    // guard zones (opt.guard): allocation base of each guarded buffer; the
+    // buffer itself starts kGuardBytes after it
+    struct GuardZone {
+        void* base;
+        size_t bytes;
+        const char* name;
+    };
+    std::vector<GuardZone> guards;
+    int guard = 0;
     const PrecOps* ops = nullptr;
     uint64_t step = 0;
 
@@ -128,13 +137,41 @@ int alloc(void** p, size_t bytes)
     return FLB_OK;
 }
 
+constexpr size_t kGuardBytes = 65536;
+constexpr unsigned char kGuardByte = 0xA5;
+
+// alloc() with guard zones on both sides when the context asks for them.
+int alloc_guarded(flb_ctx* c, void** p, size_t bytes, const char* name)
+{
+    if (!c->guard) return alloc(p, bytes);
+    if (*p) return FLB_OK;
+    void* base = nullptr;
+    int rc = alloc(&base, bytes + 2 * kGuardBytes);
+    if (rc) return rc;
+    char* user = (char*)base + kGuardBytes;
+    cudaError_t e = cudaMemsetAsync(base, kGuardByte, kGuardBytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(user + bytes, kGuardByte, kGuardBytes, c->stream);
+    if (e != cudaSuccess) {
+        cudaFree(base);
+        return fail(FLB_ECUDA, std::string("guard zones: ") + cudaGetErrorString(e));
+    }
+    c->guards.push_back({base, bytes, name});
+    *p = user;
+    return FLB_OK;
+}
+
 void free_all(flb_ctx* c)
 {
     void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
                     c->adj_work, c->adj_rows, c->adj_col, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
                     c->hs_tmp, c->sw_chol, c->sw_work, c->sw_xi};
-    for (void* p : ptrs)
-        if (p) cudaFree(p);
+    for (void* p : ptrs) {
+        bool guarded = false;
+        for (const auto& g : c->guards) guarded |= p == (char*)g.base + kGuardBytes;
+        if (p && !guarded) cudaFree(p);
+    }
+    for (const auto& g : c->guards) cudaFree(g.base);
+    c->guards.clear();
     for (double* p : c->sk_acc)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -238,6 +275,7 @@ int validate(int lattice, const int dims[3], double om_s, double om_b, double om
     if (o.precision != FLB_FP64 && o.precision != FLB_FP32 && o.precision != FLB_BF16)
         return fail(FLB_EINVAL, "unknown precision");
     if (o.check_every < 0) return fail(FLB_EINVAL, "check_every must be >= 0");
+    if (o.guard != 0 && o.guard != 1) return fail(FLB_EINVAL, "guard must be 0 or 1");
     if (fe && fe->enabled) {
         const double v[4] = {fe->A, fe->B, fe->rho_c, fe->kappa};
         for (double x : v)
@@ -264,11 +302,13 @@ void flb_default_options(flb_options* o)
     o->stream = nullptr;
     o->device = -1;
     o->check_every = 0;
+    o->guard = 0;
 }
 
 int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear, double omega_bulk,
                double omega_ghost, double kT, const flb_free_energy* fe, uint64_t seed, const flb_options* opt)
 {
+    FLB_TRACE();
     if (!out) return fail(FLB_EINVAL, "out is NULL");
     *out = nullptr;
     flb_options o;
@@ -294,6 +334,7 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
     c->ops = ops_for(o.precision);
     c->stream = (cudaStream_t)o.stream;
     c->check_every = o.check_every;
+    c->guard = o.guard;
     HostModel& m = c->m;
     m.Q = lattice;
     m.D = lattice == FLB_D2Q9 ? 2 : 3;
@@ -326,8 +367,9 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
     c->sk_count.assign(m.Q, 0);
     c->mv_sum.assign(m.Q, 0.0);
 
-    if ((rc = alloc(&c->buf[0], c->pop_bytes())) || (rc = alloc(&c->buf[1], c->pop_bytes())) ||
-        (rc = alloc(&c->drho, c->field_bytes())) || (rc = ensure_partials(c))) {
+    if ((rc = alloc_guarded(c, &c->buf[0], c->pop_bytes(), "population buffer 0")) ||
+        (rc = alloc_guarded(c, &c->buf[1], c->pop_bytes(), "population buffer 1")) ||
+        (rc = alloc_guarded(c, &c->drho, c->field_bytes(), "density field")) || (rc = ensure_partials(c))) {
         free_all(c);
         delete c;
         return rc;
@@ -370,6 +412,7 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
 
 int flb_init(flb_ctx* c, const double* rho, const double* u, int thermal_init)
 {
+    FLB_TRACE();
     if (!c) return fail(FLB_EINVAL, "ctx is NULL");
     DeviceGuard guard(c->device);
     const HostModel& m = c->m;
@@ -397,6 +440,7 @@ int flb_init(flb_ctx* c, const double* rho, const double* u, int thermal_init)
 
 int flb_step(flb_ctx* c, int nsteps)
 {
+    FLB_TRACE();
     if (!c) return fail(FLB_EINVAL, "ctx is NULL");
     if (nsteps < 0) return fail(FLB_EINVAL, "nsteps must be >= 0");
     DeviceGuard guard(c->device);
@@ -438,6 +482,7 @@ int flb_step(flb_ctx* c, int nsteps)
 
 int flb_moments(flb_ctx* c, double* out, int which)
 {
+    FLB_TRACE();
     if (!c || !out) return fail(FLB_EINVAL, "ctx or out is NULL");
     DeviceGuard guard(c->device);
     const HostModel& m = c->m;
@@ -484,6 +529,7 @@ int flb_moments(flb_ctx* c, double* out, int which)
 
 int flb_structure_factor(flb_ctx* c, double* S, int mode, int accumulate)
 {
+    FLB_TRACE();
     if (!c) return fail(FLB_EINVAL, "ctx is NULL");
     const HostModel& m = c->m;
     if (mode < 0 || mode >= m.Q) return fail(FLB_EINVAL, "mode out of range");
@@ -571,6 +617,7 @@ int heights_device(flb_ctx* c, const flb_interface_fit* f)
 
 int flb_interface_heights(flb_ctx* c, const flb_interface_fit* fit, double* h)
 {
+    FLB_TRACE();
     if (!c || !h) return fail(FLB_EINVAL, "ctx or h is NULL");
     int rc;
     if ((rc = check_fit(c, fit))) return rc;
@@ -583,6 +630,7 @@ int flb_interface_heights(flb_ctx* c, const flb_interface_fit* fit, double* h)
 
 int flb_height_spectrum(flb_ctx* c, const flb_interface_fit* fit, double* S, int accumulate)
 {
+    FLB_TRACE();
     if (!c) return fail(FLB_EINVAL, "ctx is NULL");
     int rc;
     if ((rc = check_fit(c, fit))) return rc;
@@ -610,8 +658,32 @@ int flb_height_spectrum(flb_ctx* c, const flb_interface_fit* fit, double* S, int
     return FLB_OK;
 }
 
+int flb_check_guards(flb_ctx* c)
+{
+    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
+    if (c->guards.empty()) return fail(FLB_EINVAL, "the context was created without guard zones (opt.guard = 0)");
+    DeviceGuard guard(c->device);
+    FLB_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<unsigned char> h(kGuardBytes);
+    for (const auto& g : c->guards) {
+        const char* zones[2] = {(const char*)g.base, (const char*)g.base + kGuardBytes + g.bytes};
+        for (int side = 0; side < 2; ++side) {
+            FLB_CUDA(cudaMemcpy(h.data(), zones[side], kGuardBytes, cudaMemcpyDeviceToHost));
+            for (size_t k = 0; k < kGuardBytes; ++k)
+                if (h[k] != kGuardByte) {
+                    const long long off = side == 0 ? (long long)k - (long long)kGuardBytes : (long long)(g.bytes + k);
+                    return fail(FLB_EBOUNDS, std::string("write outside the ") + g.name + " (" +
+                                                 (side == 0 ? "before its start" : "after its end") +
+                                                 "): first changed byte at offset " + std::to_string(off));
+                }
+        }
+    }
+    return FLB_OK;
+}
+
 int flb_conservation(flb_ctx* c, double out[4])
 {
+    FLB_TRACE();
     if (!c || !out) return fail(FLB_EINVAL, "ctx or out is NULL");
     DeviceGuard guard(c->device);
     return conservation(c, out);
@@ -619,6 +691,7 @@ int flb_conservation(flb_ctx* c, double out[4])
 
 int flb_get_populations(flb_ctx* c, double* f)
 {
+    FLB_TRACE();
     if (!c || !f) return fail(FLB_EINVAL, "ctx or f is NULL");
     DeviceGuard guard(c->device);
     const size_t n = (size_t)c->m.Q * c->m.V;
@@ -633,8 +706,39 @@ int flb_get_populations(flb_ctx* c, double* f)
     return FLB_OK;
 }
 
+int flb_get_sites(flb_ctx* c, const long long* sites, int n, double* f)
+{
+    FLB_TRACE();
+    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(FLB_EINVAL, "n must be >= 0");
+    if (n == 0) return FLB_OK;
+    if (!sites || !f) return fail(FLB_EINVAL, "sites or f is NULL");
+    for (int k = 0; k < n; ++k)
+        if (sites[k] < 0 || sites[k] >= c->m.V)
+            return fail(FLB_EINVAL, "site " + std::to_string(sites[k]) + " outside [0, V)");
+    DeviceGuard guard(c->device);
+    long long* d_sites = nullptr;
+    double* d = nullptr;
+    int rc = alloc((void**)&d_sites, (size_t)n * sizeof(long long));
+    if (rc) return rc;
+    if ((rc = alloc((void**)&d, (size_t)c->m.Q * n * sizeof(double)))) {
+        cudaFree(d_sites);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_sites, sites, (size_t)n * sizeof(long long), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = c->ops->get_sites(c->m, c->buf[c->cur], d_sites, n, d, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f, d, (size_t)c->m.Q * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    cudaFree(d_sites);
+    if (e != cudaSuccess) return fail(FLB_ECUDA, std::string("flb_get_sites: ") + cudaGetErrorString(e));
+    return FLB_OK;
+}
+
 int flb_set_populations(flb_ctx* c, const double* f)
 {
+    FLB_TRACE();
     if (!c || !f) return fail(FLB_EINVAL, "ctx or f is NULL");
     DeviceGuard guard(c->device);
     const size_t n = (size_t)c->m.Q * c->m.V;
@@ -651,6 +755,7 @@ int flb_set_populations(flb_ctx* c, const double* f)
 
 int flb_get_state_device(flb_ctx* c, void* g)
 {
+    FLB_TRACE();
     if (!c || !g) return fail(FLB_EINVAL, "ctx or g is NULL");
     DeviceGuard guard(c->device);
     FLB_CUDA(c->ops->pull_state(c->m, c->buf[c->cur], g, c->stream));
@@ -659,6 +764,7 @@ int flb_get_state_device(flb_ctx* c, void* g)
 
 int flb_set_state_device(flb_ctx* c, const void* g)
 {
+    FLB_TRACE();
     if (!c || !g) return fail(FLB_EINVAL, "ctx or g is NULL");
     DeviceGuard guard(c->device);
     FLB_CUDA(c->ops->push_state(c->m, g, c->buf[c->cur], c->stream));
@@ -667,6 +773,7 @@ int flb_set_state_device(flb_ctx* c, const void* g)
 
 int flb_adjoint_step(flb_ctx* c, const void* g_n, uint64_t step, const void* lam_next, void* lam, double* grad)
 {
+    FLB_TRACE();
     if (!c || !g_n || !lam_next || !lam || !grad) return fail(FLB_EINVAL, "NULL argument");
     if (c->m.Q != 19) return fail(FLB_EINVAL, "the adjoint step is implemented for D3Q19");
     if (c->prec == FLB_BF16) return fail(FLB_EINVAL, "the adjoint step needs FLB_FP64 or FLB_FP32 storage");
@@ -756,6 +863,7 @@ int flb_kernel_times(flb_ctx* c, double* ms, int* launches)
 
 int flb_save(flb_ctx* c, const char* path)
 {
+    FLB_TRACE();
     if (!c || !path) return fail(FLB_EINVAL, "ctx or path is NULL");
     DeviceGuard guard(c->device);
     std::vector<char> host(c->pop_bytes());
@@ -778,6 +886,7 @@ int flb_save(flb_ctx* c, const char* path)
 
 int flb_load(flb_ctx** out, const char* path, const flb_options* opt)
 {
+    FLB_TRACE();
     if (!out || !path) return fail(FLB_EINVAL, "out or path is NULL");
     *out = nullptr;
     FILE* fp = std::fopen(path, "rb");
@@ -840,6 +949,7 @@ const char* flb_error_string(int code)
     case FLB_EDIVERGED: return "simulation diverged (non-finite mass or momentum)";
     case FLB_ETIMEOUT: return "device wait timed out";
     case FLB_EIO: return "checkpoint I/O error";
+    case FLB_EBOUNDS: return "write outside a device buffer (guard zone overwritten)";
     default: return "unknown error";
     }
 }

@@ -278,6 +278,7 @@ int flb_batch_create(flb_batch** out, int lattice, int n, const int* dims, const
                      const double* omega_bulk, const double* omega_ghost, const double* kT, const uint64_t* seeds,
                      const flb_options* opt)
 {
+    FLB_TRACE();
     if (!out) return bfail(FLB_EINVAL, "out is NULL");
     *out = nullptr;
     if (lattice != FLB_D3Q19) return bfail(FLB_EINVAL, "batches support FLB_D3Q19");
@@ -360,6 +361,7 @@ int flb_batch_create(flb_batch** out, int lattice, int n, const int* dims, const
 
 int flb_batch_init(flb_batch* b, int thermal_init)
 {
+    FLB_TRACE();
     if (!b) return bfail(FLB_EINVAL, "batch is NULL");
     Dev guard(b->device);
     const flb::PrecOps& ops = flb::ops_fp32();
@@ -377,6 +379,7 @@ int flb_batch_init(flb_batch* b, int thermal_init)
 
 int flb_batch_step(flb_batch* b, int nsteps)
 {
+    FLB_TRACE();
     if (!b) return bfail(FLB_EINVAL, "batch is NULL");
     if (nsteps < 0) return bfail(FLB_EINVAL, "nsteps must be >= 0");
     Dev guard(b->device);
@@ -399,6 +402,7 @@ int flb_batch_step(flb_batch* b, int nsteps)
 
 int flb_batch_autotune(flb_batch* b, int* shapes_out)
 {
+    FLB_TRACE();
     if (!b) return bfail(FLB_EINVAL, "batch is NULL");
     Dev guard(b->device);
     // distinct lattice sizes
@@ -465,6 +469,7 @@ int flb_batch_autotune(flb_batch* b, int* shapes_out)
 
 int flb_batch_mode_variance(flb_batch* b, double* out)
 {
+    FLB_TRACE();
     if (!b || !out) return bfail(FLB_EINVAL, "NULL argument");
     Dev guard(b->device);
     const flb::PrecOps& ops = flb::ops_fp32();
@@ -494,6 +499,7 @@ int flb_batch_mode_variance(flb_batch* b, double* out)
 
 int flb_batch_structure_factor(flb_batch* b, int replica, double* S, int mode, int accumulate)
 {
+    FLB_TRACE();
     if (!b) return bfail(FLB_EINVAL, "batch is NULL");
     if (replica < 0 || replica >= b->n || mode < 0 || mode >= 19) return bfail(FLB_EINVAL, "replica or mode out of range");
     Dev guard(b->device);
@@ -531,6 +537,7 @@ int flb_batch_structure_factor(flb_batch* b, int replica, double* S, int mode, i
 
 int flb_batch_get_populations(flb_batch* b, int replica, double* f)
 {
+    FLB_TRACE();
     if (!b || !f) return bfail(FLB_EINVAL, "NULL argument");
     if (replica < 0 || replica >= b->n) return bfail(FLB_EINVAL, "replica out of range");
     Dev guard(b->device);

@@ -7,10 +7,23 @@
 #include <string>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/flb.h"
 
 namespace flb {
+
+// Tracing: every C-ABI call that launches GPU work opens an NVTX range named
+// after the call, so a profiler attributes each kernel to the call that issued
+// it (e.g. ncu --nvtx --nvtx-include "flb_step/").  NVTX is header-only and
+// costs a few nanoseconds per range when no profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define FLB_TRACE() ::flb::NvtxRange flb_trace_range_(__func__)
 
 // Model parameters in double; each instantiation converts to its compute type.
 struct HostModel {
@@ -56,6 +69,9 @@ struct PrecOps {
     // pre-collision deviations in the storage type, [i][s], to / from a device buffer
     cudaError_t (*pull_state)(const HostModel&, const void* src, void* out, cudaStream_t);
     cudaError_t (*push_state)(const HostModel&, const void* in, void* dst, cudaStream_t);
+    // pre-collision populations f_i at n sites (device list), out[i*n + k]
+    cudaError_t (*get_sites)(const HostModel&, const void* src, const long long* sites, int n, double* out,
+                             cudaStream_t);
 };
 
 const PrecOps& ops_fp64();

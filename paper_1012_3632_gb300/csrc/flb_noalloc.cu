@@ -62,6 +62,7 @@ __global__ void k_mode_of_populations(const double* __restrict__ f, int mode, do
 extern "C" int flb_structure_factor_noalloc(int lattice, const int dims[3], const double* f, int mode, double* S,
                                             void* stream)
 {
+    FLB_TRACE();
     if (lattice != FLB_D2Q9 && lattice != FLB_D3Q19)
         return flb::set_error(FLB_EINVAL, "lattice must be FLB_D2Q9 or FLB_D3Q19");
     if (!dims || !f || !S) return flb::set_error(FLB_EINVAL, "dims, f and S must not be NULL");

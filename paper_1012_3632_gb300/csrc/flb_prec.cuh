@@ -164,6 +164,24 @@ __global__ void k_get_pop(const S* __restrict__ src, double* __restrict__ out, d
                                (double)load_s<R>(src + (long)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i)));
 }
 
+// f_i(r_k) = w_i rho0 + g_i pulled from r_k - c_i, for a list of sites r_k.
+template <class L, class R, class S>
+__global__ void k_get_sites(const S* __restrict__ src, const long long* __restrict__ sites, int n,
+                            double* __restrict__ out, double rho0, int X, int Y, int Z)
+{
+    const long V = (long)X * Y * Z;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const long s = sites[k];
+        const int x = (int)(s % X), y = (int)((s / X) % Y), z = (int)(s / ((long)X * Y));
+        const Nbhd nb(x, y, z, X, Y, Z);
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i)
+            out[(long)i * n + k] =
+                Vel<L>::w(i) * rho0 +
+                (double)load_s<R>(src + (long)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i)));
+    }
+}
+
 template <class L, class R, class S>
 __global__ void k_set_pop(const double* __restrict__ in, S* __restrict__ dst, double rho0, int X, int Y, int Z)
 {
@@ -664,11 +682,23 @@ struct Prec {
         return cudaGetLastError();
     }
 
+    static cudaError_t get_sites(const HostModel& m, const void* src, const long long* sites, int n, double* out,
+                                 cudaStream_t st)
+    {
+        if (n <= 0) return cudaSuccess;
+        const int nb = std::min((n + 127) / 128, 152 * 4);
+        if (m.Q == 19)
+            k_get_sites<D3Q19, R, S><<<nb, 128, 0, st>>>((const S*)src, sites, n, out, m.rho0, m.X, m.Y, m.Z);
+        else
+            k_get_sites<D2Q9, R, S><<<nb, 128, 0, st>>>((const S*)src, sites, n, out, m.rho0, m.X, m.Y, m.Z);
+        return cudaGetLastError();
+    }
+
     static const PrecOps& ops()
     {
         static const PrecOps o = {(int)sizeof(S), (int)sizeof(R), density, step, init, get_pop, set_pop, moments,
                                   mu_force, mode_partials, cons_partials, mode_field, rows, needs_density,
-                                  pull_state, push_state};
+                                  pull_state, push_state, get_sites};
         return o;
     }
 };

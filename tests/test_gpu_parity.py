@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from paper_1012_3632_gb300 import BF16, D2Q9, D3Q19, FP32, FP64, MODE_VAR, MODES, RHO, U, Context, inputs
+from paper_1012_3632_gb300.flb import FLBError
 
 pytestmark = pytest.mark.gpu
 
@@ -307,3 +308,79 @@ def test_conservation_sums_are_exact_sums_of_the_state(Q, dims, prec):
     V = int(np.prod(dims))
     assert abs(cons[0] - f.sum()) <= 1e-13 * V
     assert np.abs(np.asarray(cons[1:]) - (c.T @ f).sum(axis=1)).max() <= 1e-13 * V
+
+
+@pytest.mark.parametrize("Q,dims,prec", [(19, (10, 9, 8), "fp64"), (19, (33, 5, 3), "fp32"), (9, (17, 13, 1), "bf16"),
+                                         (19, (1, 1, 1), "fp32")])
+def test_get_sites_equals_the_full_read(Q, dims, prec):
+    """flb_get_sites returns exactly the columns of flb_get_populations (first
+    and last site, repeats, random order); bad indices are refused."""
+    V = int(np.prod(dims))
+    with Context(Q, dims, 1.2, kT=1e-5, seed=4, precision=prec) as ctx:
+        ctx.init(rho=inputs.uniform_density(dims, seed=1), thermal=True)
+        ctx.step(3)
+        f = ctx.get_populations()
+        sites = np.r_[0, V - 1, np.random.default_rng(0).integers(0, V, 40), 0]
+        assert np.array_equal(ctx.get_sites(sites), f[:, sites])
+        assert ctx.get_sites([]).shape == (Q, 0)
+        for bad in ([-1], [V], [0, V + 5]):
+            with pytest.raises(FLBError):
+                ctx.get_sites(bad)
+
+
+def _sites_window_check(ctx, p, dims, steps, radius, centres, tol):
+    """Populations at the centres (read with flb_get_sites) against oracle runs
+    on periodic-free windows around them, from the uniform rest state."""
+    X, Y, Z = dims
+    glob = [c[0] + X * (c[1] + Y * c[2]) for c in centres]
+    got = ctx.get_sites(glob)
+    h = radius + 1
+    for k, cen in enumerate(centres):
+        org = tuple(c - h for c in cen)
+        win = (2 * h + 1,) * 3
+        pw = p.with_(origin=org, window=win)
+        fw = oracle.run(pw, oracle.init(pw), 0, steps)
+        s_loc = h + win[0] * (h + win[1] * h)
+        assert np.isfinite(fw[:, s_loc]).all()
+        assert np.abs(got[:, k] - fw[:, s_loc]).max() <= tol, cen
+
+
+def _free_device_bytes():
+    import torch
+    return torch.cuda.mem_get_info()[0]
+
+
+def test_max_size_bf16_ideal_sampled():
+    """The largest lattice the API accepts, V = 2048*1024*1023 = 2 145 386 496
+    sites (just below 2^31), BF16 storage (163 GB): 2 noisy steps, sampled sites
+    against oracle windows, and the total mass."""
+    dims = (2048, 1024, 1023)
+    V = int(np.prod(dims))
+    if _free_device_bytes() < 2 * 19 * 2 * V + 4 * V + 16e9:
+        pytest.skip("not enough device memory")
+    kw = dict(kT=1e-5, omega_shear=1.2, omega_bulk=1.0, omega_ghost=1.0, seed=11)
+    ctx, p = _pair(19, dims, "bf16", None, **kw)
+    with ctx:
+        ctx.init()
+        ctx.step(2)
+        centres = [(0, 0, 0), (2047, 1023, 1022), (1000, 511, 700), (5, 1020, 1)]
+        _sites_window_check(ctx, p, dims, 2, 2, centres, TOL["bf16"])
+        cons = ctx.conservation()
+    assert abs(cons[0] / V - 1.0) < 1e-6
+
+
+def test_max_size_fp32_nonideal_sampled():
+    """1024^3 non-ideal FP32 (163 GB, the z-marching fused kernel with plane
+    offsets beyond 2^31 elements): 2 steps from the uniform state, sampled
+    sites against oracle windows."""
+    dims = (1024, 1024, 1024)
+    V = int(np.prod(dims))
+    if _free_device_bytes() < 2 * 19 * 4 * V + 4 * V + 16e9:
+        pytest.skip("not enough device memory")
+    kw = dict(kT=1e-6, omega_shear=1.0, omega_bulk=1.0, omega_ghost=1.0, seed=3)
+    ctx, p = _pair(19, dims, "fp32", FE, **kw)
+    with ctx:
+        ctx.init()
+        ctx.step(2)
+        centres = [(0, 0, 0), (1023, 1023, 1023), (512, 100, 900), (3, 1022, 511)]
+        _sites_window_check(ctx, p, dims, 2, 6, centres, TOL["fp32"])
