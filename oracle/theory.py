@@ -145,7 +145,7 @@ def noise_swift(L, rho0, kT, lam_e, lam_s, lam_q, lam_eps, cs2k) -> np.ndarray:
     on the diagonal and 6 (c_s^2(k) - cs^2)(lambda_e + lambda_eps) in the
     (e, eps) corners.  The corners are printed with 12; the FDT of
     Eq. (dbe-fdt) with Eqs. (FDBE-yeo), (meq-yeo) and (f-correl-yeo), which
-    reproduces every other printed entry, gives 6 (reading of this build)."""
+    reproduces every other printed entry, gives 6, the value used here."""
     N = L.N
     X = np.zeros((9, 9))
     X[3, 3] = N[3] * (2.0 - 3.0 * cs2k) * lam_e
