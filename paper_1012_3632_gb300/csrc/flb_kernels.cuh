@@ -119,6 +119,39 @@ __device__ __forceinline__ void pull_planes(const Planes<S>& P, const Nbhd& nb, 
     }
 }
 
+// Cache-hinted FP32 loads (PTX ld.global with an L1 eviction priority and an
+// L2 prefetch size).  stream2/stream1: populations read once per step by the
+// ideal step -- not allocated in L1, the L2 fetches 256-byte sectors.
+// keep4/keep1: the fused non-ideal step's density gather, whose lines the
+// collision of the same tile pulls again two planes later -- kept in L1 with
+// the evict_last priority, 256-byte L2 fetches.
+__device__ __forceinline__ float2 ld_stream2(const float* p)
+{
+    float2 v;
+    asm("ld.global.L1::no_allocate.L2::256B.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_stream1(const float* p)
+{
+    float v;
+    asm("ld.global.L1::no_allocate.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ld_keep4(const float* p)
+{
+    float4 v;
+    asm("ld.global.L1::evict_last.L2::256B.v4.f32 {%0, %1, %2, %3}, [%4];"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float ld_keep1(const float* p)
+{
+    float v;
+    asm("ld.global.L1::evict_last.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // ---------------------------------------------------------------------------
 // Step parameters
 // ---------------------------------------------------------------------------
@@ -332,11 +365,11 @@ __global__ void __launch_bounds__(TXT* TY* TZ, MINB)
         const float* p = P.src[i] + rb[1 - Vel<L>::cy(i)][1 - Vel<L>::cz(i)];
         const int cx = Vel<L>::cx(i);
         if (cx == 0)
-            g[i] = mk2(*reinterpret_cast<const float2*>(p + x));
+            g[i] = mk2(ld_stream2(p + x));
         else if (cx > 0)
-            g[i] = F2(p[xm], p[x]);
+            g[i] = F2(ld_stream1(p + xm), ld_stream1(p + x));
         else
-            g[i] = F2(p[x + 1], p[x2]);
+            g[i] = F2(ld_stream1(p + x + 1), ld_stream1(p + x2));
     }
     const int s = x + X * (y + Y * z);
     L::template collide<false>(g, F2(0.f), F2(0.f), F2(0.f), a.c, (uint32_t)s, a.c.step);
@@ -610,17 +643,17 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
 #pragma unroll
                         for (int i = 0; i < L::Q; ++i) {
                             const float* p = P.src[i] + hy[h][1 - Vel<L>::cy(i)] + zo[1 - Vel<L>::cz(i)];
-                            const float4 v = *reinterpret_cast<const float4*>(p + hx[h][1]);
+                            const float4 v = ld_keep4(p + hx[h][1]);
                             const int cx = Vel<L>::cx(i);
                             if (cx == 0) {
                                 glo[i] = F2(v.x, v.y);
                                 ghi[i] = F2(v.z, v.w);
                             } else if (cx > 0) {
-                                glo[i] = F2(p[hx[h][0]], v.x);
+                                glo[i] = F2(ld_keep1(p + hx[h][0]), v.x);
                                 ghi[i] = F2(v.y, v.z);
                             } else {
                                 glo[i] = F2(v.y, v.z);
-                                ghi[i] = F2(v.w, p[hx[h][2]]);
+                                ghi[i] = F2(v.w, ld_keep1(p + hx[h][2]));
                             }
                         }
                         L::moments(glo, m);
@@ -702,7 +735,8 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
             }
             const F2 rho = a.c.rho0 + mk2(*reinterpret_cast<const float2*>(srho[ra] + cr));
             const F2 pre = -3.0f * rho;
-            // pull the pair (last read of these populations in this step)
+            // pull the pair (its lines were fetched by the gather of this plane;
+            // plain loads: measured faster than the last-use or evict-first hints)
             const int xm = x == 0 ? X - 1 : x - 1, x2 = x + 2 == X ? 0 : x + 2;
             const int yv[3] = {wrap_once(y - 1, Y), y, wrap_once(y + 1, Y)};
             const int zv[3] = {XY * wrap_once(z - 1, Z), XY * z, XY * wrap_once(z + 1, Z)};
@@ -712,11 +746,11 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                 const float* p = P.src[i] + X * yv[1 - Vel<L>::cy(i)] + zv[1 - Vel<L>::cz(i)];
                 const int cx = Vel<L>::cx(i);
                 if (cx == 0)
-                    g[i] = mk2(__ldlu(reinterpret_cast<const float2*>(p + x)));
+                    g[i] = mk2(*reinterpret_cast<const float2*>(p + x));
                 else if (cx > 0)
-                    g[i] = F2(__ldlu(p + xm), __ldlu(p + x));
+                    g[i] = F2(p[xm], p[x]);
                 else
-                    g[i] = F2(__ldlu(p + x + 1), __ldlu(p + x2));
+                    g[i] = F2(p[x + 1], p[x2]);
             }
             const int s = x + X * y + XY * z;
             L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
