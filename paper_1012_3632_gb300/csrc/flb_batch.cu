@@ -80,11 +80,11 @@ __global__ void __launch_bounds__(128) k_step_batch(const __grid_constant__ Batc
                 const float* p = src + (long)i * V + X * (yv[1 - Vel<L>::cy(i)] + Y * zv[1 - Vel<L>::cz(i)]);
                 const int cx = Vel<L>::cx(i);
                 if (cx == 0)
-                    g[i] = mk2(*reinterpret_cast<const float2*>(p + x));
+                    g[i] = mk2(ld_stream2(p + x));
                 else if (cx > 0)
-                    g[i] = F2(p[xm], p[x]);
+                    g[i] = F2(ld_stream1(p + xm), ld_stream1(p + x));
                 else
-                    g[i] = F2(p[x + 1], p[x2]);
+                    g[i] = F2(ld_stream1(p + x + 1), ld_stream1(p + x2));
             }
             const int s = x + X * (y + Y * z);
             L::template collide<false>(g, F2(0.f), F2(0.f), F2(0.f), B.c, (uint32_t)s, step);
