@@ -512,6 +512,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) if flush else ev0.elapsed_time(ev1)
+    z_planes, z_tuning = ctx.z_chunk()
     # per-kernel launch times: CUDA events around every launch, on a separate
     # pass so that they do not load the timed region
     n_kt = min(args.steps, 200)
@@ -588,7 +589,8 @@ def main():
                                        "achieved_gbs": gather_b * V / (kms[0] / max(kn[0], 1) * 1e-3) / 1e9
                                        if kn[0] else None},
                     "fused_step": {"launches": n_fused, "avg_ms": kms[1] / max(n_fused, 1)},
-                    "timed_with_events_over_steps": n_kt},
+                    "timed_with_events_over_steps": n_kt,
+                    "z_planes_per_block": z_planes, "z_chunk_tuned_in_warmup": not z_tuning},
         "whole_step_gbs": (fused_b + gather_b) * V / (ms_max / args.steps * 1e-3) / 1e9,
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launch,
     }

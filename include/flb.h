@@ -141,6 +141,13 @@ typedef struct {
                             64 KiB guard zones of a fixed byte pattern on both sides,
                             checked by flb_check_guards (a bounds check of the
                             kernels' writes for debugging; default 0) */
+    int z_chunk;         /* D3Q19 non-ideal step (z-marching kernels): planes of z per
+                            thread block.  0 (default): flb_step times candidate
+                            lengths on its first steps (two launches each, CUDA
+                            events, one stream synchronisation when done) and keeps
+                            the fastest; > 0: that length (at most Z).  The chunk
+                            length changes no result: every site's arithmetic is
+                            the same. */
 } flb_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -228,6 +235,11 @@ int flb_interface_heights(flb_ctx* ctx, const flb_interface_fit* fit, double* h)
  * flb_interface_heights; device memory (a few X doubles) is allocated on the
  * first call. */
 int flb_height_spectrum(flb_ctx* ctx, const flb_interface_fit* fit, double* S, int accumulate);
+
+/* Planes of z per thread block of the D3Q19 non-ideal step (opt.z_chunk):
+ * *planes = the length in use (the built-in default while tuning or for other
+ * steps), *tuning = 1 while flb_step is still timing candidates. */
+int flb_z_chunk(flb_ctx* ctx, int* planes, int* tuning);
 
 /* Bounds check of the kernels' writes (contexts created with opt.guard = 1):
  * waits for the context's stream, copies every guard zone to the host and

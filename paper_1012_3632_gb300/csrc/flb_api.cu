@@ -1,6 +1,7 @@
 // flb_api.cu -- the C ABI declared in include/flb.h: context object, buffer
 // management, step sequencing, observables, checkpoints and error reporting.
 // All compute happens in the kernels of flb_prec.cuh / flb_fft.cu.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -75,6 +76,15 @@ struct flb_ctx {
     };
     std::vector<GuardZone> guards;
     int guard = 0;
+    // z-chunk autotuning of the z-marching step (opt.z_chunk = 0): candidate
+    // lengths, the best time of each, CUDA events of the tuning launches
+    struct ZTune {
+        bool active = false;
+        std::vector<int> cand;
+        std::vector<float> best;
+        std::vector<cudaEvent_t> ev;
+        int issued = 0;
+    } zt;
     const PrecOps* ops = nullptr;
     uint64_t step = 0;
 
@@ -172,6 +182,8 @@ void free_all(flb_ctx* c)
     }
     for (const auto& g : c->guards) cudaFree(g.base);
     c->guards.clear();
+    for (cudaEvent_t e : c->zt.ev) cudaEventDestroy(e);
+    c->zt.ev.clear();
     for (double* p : c->sk_acc)
         if (p) cudaFree(p);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -239,6 +251,57 @@ int reduce_to_host(flb_ctx* c, int nrows, int ncol, double* host)
     return FLB_OK;
 }
 
+// z-chunk autotuning of the z-marching step (D3Q19 non-ideal, opt.z_chunk = 0).
+// Candidates: for every block count nc from ceil(Z/40) to ceil(Z/12) the
+// balanced length ceil(Z/nc), at most 16 of them; each is launched twice with
+// CUDA events around it and the fastest launch decides.  The steps are the
+// caller's own steps: the chunk length changes no result.
+void ztune_start(flb_ctx* c)
+{
+    const HostModel& m = c->m;
+    if (m.zchunk != 0 || m.Q != 19 || !m.nonideal || m.Z <= 16) return;
+    std::vector<int> all;
+    for (int nc = (m.Z + 39) / 40; nc <= (m.Z + 11) / 12; ++nc) {
+        const int len = (m.Z + nc - 1) / nc;
+        if (all.empty() || all.back() != len) all.push_back(len);
+    }
+    std::vector<int> cand;
+    const size_t n = std::min<size_t>(all.size(), 16);
+    for (size_t k = 0; k < n; ++k) cand.push_back(all[k * all.size() / n]);
+    if (cand.size() < 2) return;
+    std::vector<cudaEvent_t> ev(4 * cand.size());
+    for (auto& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            for (auto& f : ev)
+                if (f) cudaEventDestroy(f);
+            return;  // no tuning: the built-in default length
+        }
+    c->zt.cand = cand;
+    c->zt.best.assign(cand.size(), 3.0e38f);
+    c->zt.ev = ev;
+    c->zt.issued = 0;
+    c->zt.active = true;
+}
+
+// All tuning launches issued: wait for them, keep the fastest length.
+int ztune_finish(flb_ctx* c)
+{
+    auto& z = c->zt;
+    FLB_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < z.issued; ++k) {
+        float ms = 0.f;
+        FLB_CUDA(cudaEventElapsedTime(&ms, z.ev[2 * k], z.ev[2 * k + 1]));
+        float& b = z.best[k % z.cand.size()];
+        b = std::min(b, ms);
+    }
+    const size_t i = std::min_element(z.best.begin(), z.best.end()) - z.best.begin();
+    c->m.zchunk = z.cand[i];
+    for (cudaEvent_t e : z.ev) cudaEventDestroy(e);
+    z.ev.clear();
+    z.active = false;
+    return FLB_OK;
+}
+
 int conservation(flb_ctx* c, double out[4])
 {
     int rc = ensure_partials(c);
@@ -276,6 +339,9 @@ int validate(int lattice, const int dims[3], double om_s, double om_b, double om
         return fail(FLB_EINVAL, "unknown precision");
     if (o.check_every < 0) return fail(FLB_EINVAL, "check_every must be >= 0");
     if (o.guard != 0 && o.guard != 1) return fail(FLB_EINVAL, "guard must be 0 or 1");
+    if (o.z_chunk < 0) return fail(FLB_EINVAL, "z_chunk must be >= 0");
+    if (o.z_chunk > 0 && (dims[2] + o.z_chunk - 1) / o.z_chunk > 65535)
+        return fail(FLB_EINVAL, "z_chunk too small for the launch grid (Z / z_chunk must be <= 65535)");
     if (fe && fe->enabled) {
         const double v[4] = {fe->A, fe->B, fe->rho_c, fe->kappa};
         for (double x : v)
@@ -303,6 +369,7 @@ void flb_default_options(flb_options* o)
     o->device = -1;
     o->check_every = 0;
     o->guard = 0;
+    o->z_chunk = 0;
 }
 
 int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear, double omega_bulk,
@@ -336,6 +403,7 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
     c->check_every = o.check_every;
     c->guard = o.guard;
     HostModel& m = c->m;
+    m.zchunk = o.z_chunk;
     m.Q = lattice;
     m.D = lattice == FLB_D2Q9 ? 2 : 3;
     m.X = dims[0];
@@ -406,6 +474,7 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
         delete c;
         return fail(FLB_ECUDA, std::string("initialising the state: ") + cudaGetErrorString(e));
     }
+    ztune_start(c);
     *out = c;
     return FLB_OK;
 }
@@ -458,7 +527,21 @@ int flb_step(flb_ctx* c, int nsteps)
             if ((rc = timer_end(c, slot))) return rc;
         }
         if ((rc = timer_begin(c, 1, &slot))) return rc;
-        FLB_CUDA(c->ops->step(c->m, c->step, src, dst, c->drho, c->stream));
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        const bool tune = c->zt.active && cudaStreamIsCapturing(c->stream, &cap) == cudaSuccess &&
+                          cap == cudaStreamCaptureStatusNone;
+        if (tune) {
+            c->m.zchunk = c->zt.cand[c->zt.issued % c->zt.cand.size()];
+            FLB_CUDA(cudaEventRecord(c->zt.ev[2 * c->zt.issued], c->stream));
+        }
+        const cudaError_t se = c->ops->step(c->m, c->step, src, dst, c->drho, c->stream);
+        if (tune) {
+            c->m.zchunk = 0;
+            FLB_CUDA(se);
+            FLB_CUDA(cudaEventRecord(c->zt.ev[2 * c->zt.issued + 1], c->stream));
+            if (++c->zt.issued == (int)(2 * c->zt.cand.size()) && (rc = ztune_finish(c))) return rc;
+        }
+        FLB_CUDA(se);
         if ((rc = timer_end(c, slot))) return rc;
         c->cur ^= 1;
         c->step += 1;
@@ -655,6 +738,14 @@ int flb_height_spectrum(flb_ctx* c, const flb_interface_fit* fit, double* S, int
             for (int k = 0; k < X; ++k) S[k] *= inv;
         }
     }
+    return FLB_OK;
+}
+
+int flb_z_chunk(flb_ctx* c, int* planes, int* tuning)
+{
+    if (!c || !planes || !tuning) return fail(FLB_EINVAL, "NULL argument");
+    *planes = std::min(c->m.zchunk > 0 ? c->m.zchunk : flb::kZChunkDefault, c->m.Z);
+    *tuning = c->zt.active ? 1 : 0;
     return FLB_OK;
 }
 

@@ -25,6 +25,10 @@ struct NvtxRange {
 };
 #define FLB_TRACE() ::flb::NvtxRange flb_trace_range_(__func__)
 
+// Planes of z per thread block of the z-marching kernels unless a context sets
+// its own (flb_options.z_chunk, or the length flb_step's tuning picks).
+constexpr int kZChunkDefault = 16;
+
 // Model parameters in double; each instantiation converts to its compute type.
 struct HostModel {
     int Q, D, X, Y, Z;
@@ -39,6 +43,7 @@ struct HostModel {
     uint64_t seed;
     uint32_t replica;
     int noise_local;
+    int zchunk = 0;  // z-marching kernels: planes per block (0: the built-in default)
 };
 
 // Kernels whose code depends on the compute/storage type.  Pointers are device

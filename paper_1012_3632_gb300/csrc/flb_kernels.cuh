@@ -166,6 +166,7 @@ struct StepArgs {
     // cs^2 grad rho = sum_i w_i c_i rho(r + c_i), which cancels the LB's own
     // ideal-gas pressure gradient (Eq. (he-force)); pgrad = 0 otherwise.
     R A, B, kappa, rho0_minus_rhoc, pgrad;
+    int nzc;  // z-marching kernels: planes per block (the z extent of a block's column)
 };
 
 // ---------------------------------------------------------------------------
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(TXT* TY* TZ)
 
 // ---------------------------------------------------------------------------
 // D3Q19 non-ideal fluid with the density gather fused in: one block owns a
-// TX x TY column of sites and marches over NZ planes in z.  Iteration k pulls
+// TX x TY column of sites and marches over a.nzc planes in z.  Iteration k pulls
 // drho of plane zb+k+2 on the tile + 2-site halo (the tile interior's pulled
 // populations are re-read from L2 by the collision two planes later),
 // evaluates mu of plane zb+k+1 on the tile + 1-site halo, and collides plane
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(TXT* TY* TZ)
 // memory; the density never goes to DRAM.  Each stage appears once in the
 // loop body so that the kernel stays small in the instruction cache.
 // ---------------------------------------------------------------------------
-template <class R, class S, int TX, int TY, int NZ, int MINB>
+template <class R, class S, int TX, int TY, int MINB>
 __global__ void __launch_bounds__(TX* TY, MINB)
     k_step_march(const StepArgs<R> a, const __grid_constant__ Planes<S> P)
 {
@@ -429,8 +430,8 @@ __global__ void __launch_bounds__(TX* TY, MINB)
     const int tid = threadIdx.x + TX * threadIdx.y;
     const int X = a.X, Y = a.Y, Z = a.Z;
     const int XY = X * Y;
-    const int xb = blockIdx.x * TX, yb = blockIdx.y * TY, zb = blockIdx.z * NZ;
-    const int nz = min(NZ, Z - zb);
+    const int xb = blockIdx.x * TX, yb = blockIdx.y * TY, zb = blockIdx.z * a.nzc;
+    const int nz = min(a.nzc, Z - zb);
 
     // In-plane neighbourhood of this thread's density sites (fixed over z):
     // x - 1, x, x + 1 and the row offsets X*(y - 1), X*y, X*(y + 1).
@@ -573,7 +574,7 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 // it works on pairs and starts at xb - 2.  Excess free energy only
 // (pgrad = 0): the total-free-energy force runs through k_step_march.
 // ---------------------------------------------------------------------------
-template <int TXT, int TY, int NZ, int MINB, int GX>
+template <int TXT, int TY, int MINB, int GX>
 __global__ void __launch_bounds__(TXT* TY, MINB)
     k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<float> P)
 {
@@ -591,8 +592,8 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
     const int tid = threadIdx.x + TXT * threadIdx.y;
     const int X = a.X, Y = a.Y, Z = a.Z;
     const int XY = X * Y;
-    const int xb = blockIdx.x * 2 * TXT, yb = blockIdx.y * TY, zb = blockIdx.z * NZ;
-    const int nz = min(NZ, Z - zb);
+    const int xb = blockIdx.x * 2 * TXT, yb = blockIdx.y * TY, zb = blockIdx.z * a.nzc;
+    const int nz = min(a.nzc, Z - zb);
     const bool small = X < RX || Y < RY;
 
     // gather items of this thread (first site gx, a multiple of GX): the sites

@@ -4,6 +4,7 @@
 // flb_fp64.cu, flb_fp32.cu and flb_bf16.cu only.
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 
@@ -12,9 +13,6 @@
 
 #ifndef FLB_MARCH_MINB
 #define FLB_MARCH_MINB 3
-#endif
-#ifndef FLB_MARCH_NZ
-#define FLB_MARCH_NZ 16
 #endif
 #ifndef FLB_MARCH_TY
 #define FLB_MARCH_TY 8
@@ -87,6 +85,7 @@ StepArgs<R> make_args(const HostModel& m, uint64_t step)
     a.kappa = R(m.kappa);
     a.rho0_minus_rhoc = R(m.rho0 - m.rho_c);
     a.pgrad = R(m.nonideal && m.total ? 1 : 0);
+    a.nzc = std::min(m.zchunk > 0 ? m.zchunk : kZChunkDefault, m.Z);
     return a;
 }
 
@@ -494,25 +493,26 @@ struct Prec {
             if (m.nonideal) {
                 if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
                     if (m.X % 2 == 0 && FLB_PACKED && !m.total) {
-                        constexpr int TXT = 16, TY = FLB_MARCH2_TY, NZ = FLB_MARCH_NZ;
+                        constexpr int TXT = 16, TY = FLB_MARCH2_TY;
                         const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                         const dim3 b(TXT, TY, 1);
-                        const dim3 g((m.X + 2 * TXT - 1) / (2 * TXT), (m.Y + TY - 1) / TY, (m.Z + NZ - 1) / NZ);
+                        const dim3 g((m.X + 2 * TXT - 1) / (2 * TXT), (m.Y + TY - 1) / TY,
+                                     (m.Z + a.nzc - 1) / a.nzc);
                         // density gather by 16-byte quads when rows are 16-byte aligned
                         if (m.X % 4 == 0)
-                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, 4>
+                            k_step_march2<TXT, TY, FLB_MARCH2_MINB, 4>
                                 <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                         else
-                            k_step_march2<TXT, TY, NZ, FLB_MARCH2_MINB, 2>
+                            k_step_march2<TXT, TY, FLB_MARCH2_MINB, 2>
                                 <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                         return cudaGetLastError();
                     }
                 }
-                constexpr int TX = 32, TY = FLB_MARCH_TY, NZ = FLB_MARCH_NZ;
+                constexpr int TX = 32, TY = FLB_MARCH_TY;
                 const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                 const dim3 b(TX, TY, 1);
-                const dim3 g((m.X + TX - 1) / TX, (m.Y + TY - 1) / TY, (m.Z + NZ - 1) / NZ);
-                k_step_march<R, S, TX, TY, NZ, (sizeof(R) == 8 ? 1 : FLB_MARCH_MINB)>
+                const dim3 g((m.X + TX - 1) / TX, (m.Y + TY - 1) / TY, (m.Z + a.nzc - 1) / a.nzc);
+                k_step_march<R, S, TX, TY, (sizeof(R) == 8 ? 1 : FLB_MARCH_MINB)>
                     <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                 return cudaGetLastError();
             }

@@ -29,7 +29,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 EXPORTS = [
     "flb_default_options", "flb_create", "flb_init", "flb_step", "flb_moments", "flb_structure_factor",
     "flb_snapshot_count", "flb_reset_accumulators", "flb_conservation", "flb_get_populations",
-    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
+    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_z_chunk", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
     "flb_get_info", "flb_kernel_timing", "flb_kernel_times", "flb_save", "flb_load", "flb_error_string",
     "flb_last_error", "flb_destroy", "flb_structure_factor_noalloc",
     "flb_batch_create", "flb_batch_init", "flb_batch_step", "flb_batch_autotune", "flb_batch_mode_variance",
@@ -82,7 +82,7 @@ def landau_free_energy(rho_l: float, rho_v: float, beta: float, kappa: float) ->
 class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rho0", ctypes.c_double), ("replica", ctypes.c_uint32),
                 ("noise_rho_local", ctypes.c_int), ("stream", ctypes.c_void_p), ("device", ctypes.c_int),
-                ("check_every", ctypes.c_int), ("guard", ctypes.c_int)]
+                ("check_every", ctypes.c_int), ("guard", ctypes.c_int), ("z_chunk", ctypes.c_int)]
 
 
 _lib = None
@@ -112,6 +112,7 @@ def lib():
         "flb_set_populations": (ctypes.c_int, [vp, dp]),
         "flb_get_sites": (ctypes.c_int, [vp, P(ctypes.c_longlong), ctypes.c_int, dp]),
         "flb_check_guards": (ctypes.c_int, [vp]),
+        "flb_z_chunk": (ctypes.c_int, [vp, ip, ip]),
         "flb_get_step": (ctypes.c_int, [vp, P(ctypes.c_uint64)]),
         "flb_set_step": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "flb_set_stream": (ctypes.c_int, [vp, vp]),
@@ -168,7 +169,7 @@ def _f64(a, n: int, name: str) -> np.ndarray:
 
 
 def options(precision="fp32", rho0=1.0, replica=0, noise_rho_local=True, stream=None, device=-1,
-            check_every=0, guard=False) -> Options:
+            check_every=0, guard=False, z_chunk=0) -> Options:
     o = Options()
     lib().flb_default_options(ctypes.byref(o))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -179,6 +180,7 @@ def options(precision="fp32", rho0=1.0, replica=0, noise_rho_local=True, stream=
     o.device = device
     o.check_every = check_every
     o.guard = int(guard)
+    o.z_chunk = int(z_chunk)
     return o
 
 
@@ -242,6 +244,12 @@ class Context:
         f = np.empty((self.Q, self.V))
         _check(lib().flb_get_populations(self._h, _dptr(f)))
         return f
+
+    def z_chunk(self):
+        """(planes of z per block of the non-ideal D3Q19 step, still tuning?)"""
+        n, t = ctypes.c_int(), ctypes.c_int()
+        _check(lib().flb_z_chunk(self._h, ctypes.byref(n), ctypes.byref(t)))
+        return n.value, bool(t.value)
 
     def check_guards(self):
         """Raise FLBError (FLB_EBOUNDS) if a kernel wrote outside a guarded buffer."""

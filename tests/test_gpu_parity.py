@@ -384,3 +384,30 @@ def test_max_size_fp32_nonideal_sampled():
         ctx.step(2)
         centres = [(0, 0, 0), (1023, 1023, 1023), (512, 100, 900), (3, 1022, 511)]
         _sites_window_check(ctx, p, dims, 2, 6, centres, TOL["fp32"])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_z_chunk_changes_no_result(prec):
+    """Planes of z per block of the z-marching non-ideal step -- fixed (1, 3, 7,
+    16, Z) or tuned by flb_step on its first launches (0) -- leave every
+    population bitwise the same; the tuned run agrees with the oracle."""
+    dims = (24, 20, 70)
+    rho = inputs.uniform_density(dims, seed=4)
+    kw = dict(kT=1e-6, omega_shear=1.1, omega_bulk=1.0, omega_ghost=1.2, seed=9)
+    out = []
+    for zc in (0, 1, 3, 7, 16, 70):
+        with Context(19, dims, precision=prec, free_energy=FE, z_chunk=zc, **kw) as ctx:
+            ctx.init(rho=rho)
+            ctx.step(30)
+            planes, tuning = ctx.z_chunk()
+            assert not tuning and 1 <= planes <= 70
+            if zc:
+                assert planes == zc
+            out.append(ctx.get_populations())
+    for f in out[1:]:
+        assert np.array_equal(f, out[0])
+    p = oracle.Params(Q=19, dims=dims, nonideal=True, **FE, **kw)
+    want = oracle.run(p, oracle.init(p, rho=rho), 0, 30)
+    assert np.abs(out[0] - want).max() <= TOL[prec]
+    with pytest.raises(FLBError):
+        Context(19, dims, precision=prec, free_energy=FE, z_chunk=-1, **kw)
