@@ -287,9 +287,10 @@ void ztune_start(flb_ctx* c)
 int ztune_finish(flb_ctx* c)
 {
     auto& z = c->zt;
-    FLB_CUDA(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < z.issued; ++k) {
         float ms = 0.f;
+        // the launches may span a flb_set_stream: wait on each launch's own event
+        FLB_CUDA(cudaEventSynchronize(z.ev[2 * k + 1]));
         FLB_CUDA(cudaEventElapsedTime(&ms, z.ev[2 * k], z.ev[2 * k + 1]));
         float& b = z.best[k % z.cand.size()];
         b = std::min(b, ms);
