@@ -62,6 +62,14 @@ WORKLOADS = {
                                "beta (rho-0.5)^2 (rho-1)^2, beta=0.1, kappa=0.08, modified-equilibrium model "
                                "(pressure in the equilibrium, e/eps noise coloured by FFT), kT=1e-7, tau=1, "
                                "FP32 deviations"),
+    "nonideal256_bf16": dict(lattice=19, dims=(256, 256, 256), precision="bf16", fe=FE, kT=1e-6,
+                             omega=(1.0, 1.0, 1.0), seed=3,
+                             name="D3Q19 force-based non-ideal fluid, 256^3, BF16 deviations (FP32 arithmetic), "
+                                  "parameters of the FP32 256^3 workload"),
+    "ideal256_bf16": dict(lattice=19, dims=(256, 256, 256), precision="bf16", fe=None, kT=1e-5,
+                          omega=(1.2, 1.0, 1.0), seed=2,
+                          name="D3Q19 ideal gas, 256^3, BF16 deviations (FP32 arithmetic), kT=1e-5, "
+                               "omega=(1.2, 1.0, 1.0), shear wave + thermal start"),
     "ideal128": dict(lattice=19, dims=(128, 128, 128), precision="fp32", fe=None, kT=1e-5,
                      omega=(1.2, 1.0, 1.0), seed=2,
                      name="D3Q19 ideal gas, 128^3 periodic, FP32 deviations, kT=1e-5, "
@@ -155,7 +163,7 @@ def initial_density(wl, dims):
 
 def kernel_name(wl):
     """The step kernel the library launches for this workload."""
-    packed = wl["precision"] == "fp32" and wl["dims"][0] % 2 == 0 and wl["lattice"] == 19
+    packed = wl["precision"] in ("fp32", "bf16") and wl["dims"][0] % 2 == 0 and wl["lattice"] == 19
     if wl["fe"] and wl["fe"].get("model", 0) == 1:
         return "k_step_swift"
     if wl["fe"] and wl["lattice"] == 19:

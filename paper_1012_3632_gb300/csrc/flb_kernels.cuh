@@ -152,6 +152,64 @@ __device__ __forceinline__ float ld_keep1(const float* p)
     return v;
 }
 
+// Storage access of the two-sites-per-thread kernels, FP32 in registers:
+// S = float, or __nv_bfloat16 (a bf16 widens to FP32 exactly by a 16-bit
+// shift; stores round to nearest even, as store_s does).  stream: the ideal
+// step's hints above; keep: the density gather's; plain: the collision's pull.
+template <class S>
+struct Packed;
+template <>
+struct Packed<float> {
+    static __device__ __forceinline__ float2 stream2(const float* p) { return ld_stream2(p); }
+    static __device__ __forceinline__ float stream1(const float* p) { return ld_stream1(p); }
+    static __device__ __forceinline__ float4 keep4(const float* p) { return ld_keep4(p); }
+    static __device__ __forceinline__ float keep1(const float* p) { return ld_keep1(p); }
+    static __device__ __forceinline__ float2 plain2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+    static __device__ __forceinline__ float plain1(const float* p) { return *p; }
+    static __device__ __forceinline__ void store2(float* p, float2 v) { __stcs(reinterpret_cast<float2*>(p), v); }
+};
+template <>
+struct Packed<__nv_bfloat16> {
+    using B = __nv_bfloat16;
+    static __device__ __forceinline__ float lo(uint32_t u) { return __uint_as_float(u << 16); }
+    static __device__ __forceinline__ float hi(uint32_t u) { return __uint_as_float(u & 0xffff0000u); }
+    static __device__ __forceinline__ float2 stream2(const B* p)
+    {
+        uint32_t u;
+        asm("ld.global.L1::no_allocate.L2::256B.b32 %0, [%1];" : "=r"(u) : "l"(p));
+        return make_float2(lo(u), hi(u));
+    }
+    static __device__ __forceinline__ float stream1(const B* p)
+    {
+        unsigned short u;
+        asm("ld.global.L1::no_allocate.L2::256B.b16 %0, [%1];" : "=h"(u) : "l"(p));
+        return lo(u);
+    }
+    static __device__ __forceinline__ float4 keep4(const B* p)
+    {
+        uint32_t a, b;
+        asm("ld.global.L1::evict_last.L2::256B.v2.b32 {%0, %1}, [%2];" : "=r"(a), "=r"(b) : "l"(p));
+        return make_float4(lo(a), hi(a), lo(b), hi(b));
+    }
+    static __device__ __forceinline__ float keep1(const B* p)
+    {
+        unsigned short u;
+        asm("ld.global.L1::evict_last.L2::256B.b16 %0, [%1];" : "=h"(u) : "l"(p));
+        return lo(u);
+    }
+    static __device__ __forceinline__ float2 plain2(const B* p)
+    {
+        const uint32_t u = *reinterpret_cast<const uint32_t*>(p);
+        return make_float2(lo(u), hi(u));
+    }
+    static __device__ __forceinline__ float plain1(const B* p) { return __bfloat162float(*p); }
+    static __device__ __forceinline__ void store2(B* p, float2 v)
+    {
+        const __nv_bfloat162 b = __float22bfloat162_rn(v);
+        __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<const unsigned int*>(&b));
+    }
+};
+
 // ---------------------------------------------------------------------------
 // Step parameters
 // ---------------------------------------------------------------------------
@@ -336,16 +394,17 @@ __global__ void __launch_bounds__(TX* TY)
 }
 
 // ---------------------------------------------------------------------------
-// Ideal gas, FP32 storage, two sites (x, x+1) per thread with packed FP32
-// arithmetic (F2).  X must be even: a thread's pair then never straddles a row
-// and its populations at (x, x+1) are 8-byte aligned.  Pulls along c_x = 0 are
+// Ideal gas, FP32 or BF16 storage, two sites (x, x+1) per thread with packed
+// FP32 arithmetic (F2).  X must be even: a thread's pair then never straddles a
+// row and its populations at (x, x+1) are aligned to the pair's size.  Pulls along c_x = 0 are
 // single 8-byte loads; along c_x = +-1 the pair comes from (x-1, x) or
 // (x+1, x+2).  Block = TXT x TY x TZ threads covering 2 TXT x TY x TZ sites.
 // ---------------------------------------------------------------------------
-template <class L, int TXT, int TY, int TZ, int MINB = 1>
+template <class L, class S, int TXT, int TY, int TZ, int MINB = 1>
 __global__ void __launch_bounds__(TXT* TY* TZ, MINB)
-    k_step2(const StepArgs<float> a, const __grid_constant__ Planes<float> P)
+    k_step2(const StepArgs<float> a, const __grid_constant__ Planes<S> P)
 {
+    using A = Packed<S>;
     const int x = 2 * (blockIdx.x * TXT + threadIdx.x);
     const int y = blockIdx.y * TY + threadIdx.y;
     const int z = blockIdx.z * TZ + threadIdx.z;
@@ -363,19 +422,19 @@ __global__ void __launch_bounds__(TXT* TY* TZ, MINB)
     F2 g[L::Q];
 #pragma unroll
     for (int i = 0; i < L::Q; ++i) {
-        const float* p = P.src[i] + rb[1 - Vel<L>::cy(i)][1 - Vel<L>::cz(i)];
+        const S* p = P.src[i] + rb[1 - Vel<L>::cy(i)][1 - Vel<L>::cz(i)];
         const int cx = Vel<L>::cx(i);
         if (cx == 0)
-            g[i] = mk2(ld_stream2(p + x));
+            g[i] = mk2(A::stream2(p + x));
         else if (cx > 0)
-            g[i] = F2(ld_stream1(p + xm), ld_stream1(p + x));
+            g[i] = F2(A::stream1(p + xm), A::stream1(p + x));
         else
-            g[i] = F2(ld_stream1(p + x + 1), ld_stream1(p + x2));
+            g[i] = F2(A::stream1(p + x + 1), A::stream1(p + x2));
     }
     const int s = x + X * (y + Y * z);
     L::template collide<false>(g, F2(0.f), F2(0.f), F2(0.f), a.c, (uint32_t)s, a.c.step);
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i) __stcs(reinterpret_cast<float2*>(P.dst[i] + s), g[i].v);
+    for (int i = 0; i < L::Q; ++i) A::store2(P.dst[i] + s, g[i].v);
 }
 
 // Density gather for site pairs (x, x+1), packed FP32; X even.
@@ -564,20 +623,22 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 
 
 // ---------------------------------------------------------------------------
-// Packed-FP32 form of k_step_march: each thread owns the two sites (x, x+1)
-// of its column pair, and every stage (density gather, mu, F, collision) works
-// on site pairs with FADD2/FMUL2/FFMA2.  X must be even.  Same algorithm and
-// ring layout as k_step_march; the density and mu planes are stored as float2
-// pairs.  GX = 4 (X % 4 == 0): the density gather works on quads of sites, one
-// 16-byte load per direction plus one 4-byte load for c_x = +-1, and the
-// density plane starts at x = xb - 4 so that its quads stay aligned; GX = 2:
-// it works on pairs and starts at xb - 2.  Excess free energy only
-// (pgrad = 0): the total-free-energy force runs through k_step_march.
+// Packed-FP32 form of k_step_march (FP32 or BF16 storage S): each thread owns
+// the two sites (x, x+1) of its column pair, and every stage (density gather,
+// mu, F, collision) works on site pairs with FADD2/FMUL2/FFMA2.  X must be
+// even.  Same algorithm and ring layout as k_step_march; the density and mu
+// planes are stored as float2 pairs.  GX = 4 (X % 4 == 0): the density gather
+// works on quads of sites, one 4-element load per direction plus one
+// 1-element load for c_x = +-1, and the density plane starts at x = xb - 4 so
+// that its quads stay aligned; GX = 2: it works on pairs and starts at
+// xb - 2.  Excess free energy only (pgrad = 0): the total-free-energy force
+// runs through k_step_march.
 // ---------------------------------------------------------------------------
-template <int TXT, int TY, int MINB, int GX>
+template <class S, int TXT, int TY, int MINB, int GX>
 __global__ void __launch_bounds__(TXT* TY, MINB)
-    k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<float> P)
+    k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<S> P)
 {
+    using A = Packed<S>;
     using L = D3Q19;
     constexpr bool QUAD = GX == 4;
     constexpr int NT = TXT * TY;
@@ -643,18 +704,18 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                         F2 glo[L::Q], ghi[L::Q], m[L::Q];
 #pragma unroll
                         for (int i = 0; i < L::Q; ++i) {
-                            const float* p = P.src[i] + hy[h][1 - Vel<L>::cy(i)] + zo[1 - Vel<L>::cz(i)];
-                            const float4 v = ld_keep4(p + hx[h][1]);
+                            const S* p = P.src[i] + hy[h][1 - Vel<L>::cy(i)] + zo[1 - Vel<L>::cz(i)];
+                            const float4 v = A::keep4(p + hx[h][1]);
                             const int cx = Vel<L>::cx(i);
                             if (cx == 0) {
                                 glo[i] = F2(v.x, v.y);
                                 ghi[i] = F2(v.z, v.w);
                             } else if (cx > 0) {
-                                glo[i] = F2(ld_keep1(p + hx[h][0]), v.x);
+                                glo[i] = F2(A::keep1(p + hx[h][0]), v.x);
                                 ghi[i] = F2(v.y, v.z);
                             } else {
                                 glo[i] = F2(v.y, v.z);
-                                ghi[i] = F2(v.w, ld_keep1(p + hx[h][2]));
+                                ghi[i] = F2(v.w, A::keep1(p + hx[h][2]));
                             }
                         }
                         L::moments(glo, m);
@@ -666,14 +727,14 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                         F2 g[L::Q], m[L::Q];
 #pragma unroll
                         for (int i = 0; i < L::Q; ++i) {
-                            const float* p = P.src[i] + hy[h][1 - Vel<L>::cy(i)] + zo[1 - Vel<L>::cz(i)];
+                            const S* p = P.src[i] + hy[h][1 - Vel<L>::cy(i)] + zo[1 - Vel<L>::cz(i)];
                             const int cx = Vel<L>::cx(i);
                             if (cx == 0)
-                                g[i] = mk2(*reinterpret_cast<const float2*>(p + hx[h][1]));
+                                g[i] = mk2(A::plain2(p + hx[h][1]));
                             else if (cx > 0)
-                                g[i] = F2(p[hx[h][0]], p[hx[h][1]]);
+                                g[i] = F2(A::plain1(p + hx[h][0]), A::plain1(p + hx[h][1]));
                             else
-                                g[i] = F2(p[hx[h][1] + 1], p[hx[h][2]]);
+                                g[i] = F2(A::plain1(p + hx[h][1] + 1), A::plain1(p + hx[h][2]));
                         }
                         L::moments(g, m);
                         *reinterpret_cast<float2*>(out + 2 * e) = m[0].v;
@@ -744,19 +805,19 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
             F2 g[L::Q];
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
-                const float* p = P.src[i] + X * yv[1 - Vel<L>::cy(i)] + zv[1 - Vel<L>::cz(i)];
+                const S* p = P.src[i] + X * yv[1 - Vel<L>::cy(i)] + zv[1 - Vel<L>::cz(i)];
                 const int cx = Vel<L>::cx(i);
                 if (cx == 0)
-                    g[i] = mk2(*reinterpret_cast<const float2*>(p + x));
+                    g[i] = mk2(A::plain2(p + x));
                 else if (cx > 0)
-                    g[i] = F2(p[xm], p[x]);
+                    g[i] = F2(A::plain1(p + xm), A::plain1(p + x));
                 else
-                    g[i] = F2(p[x + 1], p[x2]);
+                    g[i] = F2(A::plain1(p + x + 1), A::plain1(p + x2));
             }
             const int s = x + X * y + XY * z;
             L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i) __stcs(reinterpret_cast<float2*>(P.dst[i] + s), g[i].v);
+            for (int i = 0; i < L::Q; ++i) A::store2(P.dst[i] + s, g[i].v);
         }
         ra = ra1;
         mb = mb1;

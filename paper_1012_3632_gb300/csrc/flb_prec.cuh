@@ -446,6 +446,9 @@ __global__ void k_mode_field(const S* __restrict__ src, int mode, double2* __res
 // ---------------------------------------------------------------------------
 template <class R, class S>
 struct Prec {
+    // FP32 arithmetic on FP32 or BF16 storage: the two-sites-per-thread kernels
+    static constexpr bool kPackedStorage =
+        std::is_same<R, float>::value && (std::is_same<S, float>::value || std::is_same<S, __nv_bfloat16>::value);
     template <class L>
     static cudaError_t density_l(const HostModel& m, const void* pop, void* drho, cudaStream_t st)
     {
@@ -491,19 +494,19 @@ struct Prec {
         }
         if (m.Q == 19) {
             if (m.nonideal) {
-                if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+                if constexpr (kPackedStorage) {
                     if (m.X % 2 == 0 && FLB_PACKED && !m.total) {
                         constexpr int TXT = 16, TY = FLB_MARCH2_TY;
                         const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                         const dim3 b(TXT, TY, 1);
                         const dim3 g((m.X + 2 * TXT - 1) / (2 * TXT), (m.Y + TY - 1) / TY,
                                      (m.Z + a.nzc - 1) / a.nzc);
-                        // density gather by 16-byte quads when rows are 16-byte aligned
+                        // density gather by quads of sites when rows hold whole quads
                         if (m.X % 4 == 0)
-                            k_step_march2<TXT, TY, FLB_MARCH2_MINB, 4>
+                            k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 4>
                                 <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                         else
-                            k_step_march2<TXT, TY, FLB_MARCH2_MINB, 2>
+                            k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 2>
                                 <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                         return cudaGetLastError();
                     }
@@ -516,13 +519,13 @@ struct Prec {
                     <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                 return cudaGetLastError();
             }
-            if constexpr (std::is_same<R, float>::value && std::is_same<S, float>::value) {
+            if constexpr (kPackedStorage) {
                 if (m.X % 2 == 0 && FLB_PACKED) {
                     constexpr int TXT = FLB_STEP2_TXT, TY = FLB_STEP2_TY, TZ = FLB_STEP2_TZ;
                     const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                     const dim3 b(TXT, TY, TZ);
                     const dim3 g((m.X / 2 + TXT - 1) / TXT, (m.Y + TY - 1) / TY, (m.Z + TZ - 1) / TZ);
-                    k_step2<D3Q19, TXT, TY, TZ, FLB_STEP2_MINB>
+                    k_step2<D3Q19, S, TXT, TY, TZ, FLB_STEP2_MINB>
                         <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                     return cudaGetLastError();
                 }

@@ -112,6 +112,18 @@ def test_bf16_storage():
     assert np.abs(got - want).max() <= TOL["bf16"]
 
 
+@pytest.mark.parametrize("dims,fe", [((24, 10, 9), FE), ((18, 10, 9), FE), ((17, 10, 9), FE), ((15, 12, 10), None),
+                                     ((4, 5, 3), FE)])
+def test_bf16_storage_paths(dims, fe):
+    """BF16 storage through every D3Q19 step kernel: the two-sites-per-thread
+    non-ideal step with quad (X % 4 = 0) and pair gathers, the one-site kernels
+    for odd X, ideal and non-ideal, against the FP64 oracle after 20 steps."""
+    rho = inputs.uniform_density(dims, seed=3) if fe else None
+    got, want = _run_both(19, dims, "bf16", 20, fe=fe, rho=rho, thermal=fe is None, kT=1e-5, omega_shear=1.1,
+                          omega_bulk=1.0, omega_ghost=1.2, seed=6)
+    assert np.abs(got - want).max() <= TOL["bf16"]
+
+
 @pytest.mark.parametrize("Q,dims", [(19, (6, 5, 4)), (9, (7, 5, 1))])
 def test_init_parity(Q, dims):
     D = 2 if Q == 9 else 3
