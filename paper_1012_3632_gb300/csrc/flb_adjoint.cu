@@ -156,20 +156,20 @@ __device__ __forceinline__ void collide_vjp(const R gn[19], const R F[3], const 
 
 __device__ __forceinline__ long blin() { return blockIdx.x + (long)gridDim.x * (blockIdx.y + (long)gridDim.y * blockIdx.z); }
 
+// Block sums of NV per-thread values: warp sums in the compute type (32
+// terms; FP64 arithmetic per thread would run on GB300's slow FP64 pipe),
+// then FP64 across the warps of the block and, in sum_columns, across blocks.
 template <int NV, class R>
 __device__ __forceinline__ void block_rows(R v[NV], double* __restrict__ row)
 {
     __shared__ double red[32][NV];
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
     const int nthr = blockDim.x * blockDim.y * blockDim.z;
-    double d[NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-        d[k] = (double)v[k];
-        for (int o = 16; o > 0; o >>= 1) d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
-    }
+    for (int k = 0; k < NV; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if ((tid & 31) == 0)
-        for (int k = 0; k < NV; ++k) red[tid >> 5][k] = d[k];
+        for (int k = 0; k < NV; ++k) red[tid >> 5][k] = (double)v[k];
     __syncthreads();
     for (int k = tid; k < NV; k += nthr) {
         double acc = 0.0;
@@ -350,8 +350,11 @@ cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, 
     const dim3 b(32, 4, 2);
     const dim3 g((m.X + 31) / 32, (m.Y + 3) / 4, (m.Z + 1) / 2);
     const int nrows = (int)(g.x * g.y * g.z);
-    cudaError_t e = cudaMemsetAsync(rows, 0, (size_t)nrows * 6 * sizeof(double), st);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    // every block writes columns 0-2 (collision) and, for the non-ideal fluid,
+    // 3-5 (free-energy parameters); the ideal gas leaves 3-5 at zero
+    if (!m.nonideal && (e = cudaMemsetAsync(rows, 0, (size_t)nrows * 6 * sizeof(double), st)) != cudaSuccess)
+        return e;
     if (m.nonideal) {
         k_adj_rho<R><<<(unsigned)std::min<long>((V + 255) / 256, 152 * 16), 256, 0, st>>>(gn, drho, V);
         StepArgs<R> sa{};
