@@ -290,6 +290,18 @@ int flb_set_state_device(flb_ctx* ctx, const void* g);
  * use.  Enqueued on the context's stream. */
 int flb_adjoint_step(flb_ctx* ctx, const void* g_n, uint64_t step, const void* lam_next, void* lam, double* grad);
 
+/* One checkpoint segment of the reverse pass in a single call.  From the
+ * state g_start at time step0, recompute the states at step0 .. step0+n-1
+ * (n >= 1) into `states`, a caller-owned device array of n*19*V elements of
+ * the storage type (states[k*19*V + i*V + s]), then apply flb_adjoint_step
+ * from time step0+n-1 down to step0.  lam: device, 19*V elements, holds
+ * dJ/dg at time step0+n on entry and dJ/dg at time step0 on return; grad[6]
+ * accumulates as in flb_adjoint_step.  The recomputation runs the context's
+ * own step (its state and step counter end at time step0+n-1).  Errors and
+ * restrictions as flb_adjoint_step; enqueued on the context's stream. */
+int flb_adjoint_segment(flb_ctx* ctx, const void* g_start, uint64_t step0, int n, void* states, void* lam,
+                        double* grad);
+
 /* Step counter (the time index keying the collision noise). */
 int flb_get_step(flb_ctx* ctx, uint64_t* step);
 int flb_set_step(flb_ctx* ctx, uint64_t step);

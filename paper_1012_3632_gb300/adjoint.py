@@ -7,7 +7,8 @@ dtype of the storage precision) and keeps a copy of the state every ``every``
 steps.  The backward pass walks the segments in reverse: it recomputes the
 states of a segment from its checkpoint (the Philox noise is a pure function
 of seed, site and step, so the recomputed trajectory is identical) and applies
-``flb_adjoint_step`` from the last step of the segment to the first.  The
+the adjoint step from the last step of the segment to the first, both in one
+``flb_adjoint_segment`` call per segment.  The
 parameters theta = (omega_shear, omega_bulk, omega_ghost, kappa, A, B) get
 their gradients from the same adjoint steps.
 
@@ -46,9 +47,9 @@ class FLBRun(torch.autograd.Function):
         ctx.set_state_device(g0.data_ptr())
         ctx.step_count = 0
         ckpts = [g0.clone()]
-        for n in range(nsteps):
-            ctx.step(1)
-            if (n + 1) % every == 0 and n + 1 < nsteps:
+        for start in range(0, nsteps, every):
+            ctx.step(min(every, nsteps - start))
+            if start + every < nsteps:
                 c = torch.empty_like(g0)
                 ctx.get_state_device(c.data_ptr())
                 ckpts.append(c)
@@ -67,20 +68,13 @@ class FLBRun(torch.autograd.Function):
         lam = lamN.contiguous().clone()
         grad = torch.zeros(6, dtype=torch.float64, device=lam.device)
         nseg = (nsteps + every - 1) // every
+        states = torch.empty((min(every, nsteps),) + tuple(lam.shape), dtype=lam.dtype, device=lam.device)
         for seg in reversed(range(nseg)):
             start, end = seg * every, min((seg + 1) * every, nsteps)
-            states = [fctx.ckpts[seg]]
-            ctx.set_state_device(states[0].data_ptr())
-            ctx.step_count = start
-            for _ in range(start, end - 1):
-                ctx.step(1)
-                s = torch.empty_like(lam)
-                ctx.get_state_device(s.data_ptr())
-                states.append(s)
-            for n in reversed(range(start, end)):
-                nxt = torch.empty_like(lam)
-                ctx.adjoint_step(states[n - start].data_ptr(), n, lam.data_ptr(), nxt.data_ptr(), grad.data_ptr())
-                lam = nxt
+            # recompute the segment from its checkpoint and run its adjoint steps
+            # backwards (flb_adjoint_segment); lam is updated in place
+            ctx.adjoint_segment(fctx.ckpts[seg].data_ptr(), start, end - start, states.data_ptr(), lam.data_ptr(),
+                                grad.data_ptr())
         ctx.close()
         dtype, device = fctx.theta_meta
         return lam, grad.to(dtype=dtype, device=device), None

@@ -191,10 +191,12 @@ __global__ void k_adj_rho(const R* __restrict__ gn, R* __restrict__ drho, long V
     }
 }
 
+// rb_next (or NULL): the density part of lam_next kept apart by the previous
+// adjoint step of a segment; lam_next + rb_next is the full adjoint state.
 template <class R>
 __global__ void k_adj_collide(const AdjArgs<R> a, uint32_t step, const R* __restrict__ gn, const R* __restrict__ F,
-                              const R* __restrict__ lam_next, R* __restrict__ lam, R* __restrict__ Fbar,
-                              double* __restrict__ rows)
+                              const R* __restrict__ lam_next, const R* __restrict__ rb_next, R* __restrict__ lam,
+                              R* __restrict__ Fbar, double* __restrict__ rows)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -209,7 +211,8 @@ __global__ void k_adj_collide(const AdjArgs<R> a, uint32_t step, const R* __rest
         for (int i = 0; i < 19; ++i) {
             g[i] = gn[(long)i * V + s];
             // streaming moved the post-collision population i from r to r + c_i
-            lb[i] = lam_next[(long)i * V + nb.src(-Vel<L>::cx(i), -Vel<L>::cy(i), -Vel<L>::cz(i))];
+            const int q = nb.src(-Vel<L>::cx(i), -Vel<L>::cy(i), -Vel<L>::cz(i));
+            lb[i] = rb_next ? lam_next[(long)i * V + q] + rb_next[q] : lam_next[(long)i * V + q];
         }
         if (a.nonideal)
             for (int d = 0; d < 3; ++d) Fs[d] = F[d * V + s];
@@ -257,11 +260,13 @@ __global__ void k_adj_mu(const AdjArgs<R> a, const R* __restrict__ drho, const R
     rb1[s] = fg / rho + a.pgrad * accp;
 }
 
-// rhobar = rb1 + psi''(rho) mubar - kappa lap(mubar), added to every population;
+// rhobar = rb1 + psi''(rho) mubar - kappa lap(mubar), added to every population
+// (or, with rb_out, stored for the next adjoint step of a segment to add);
 // kappa, A, B gradients
 template <class R>
 __global__ void k_adj_rho(const AdjArgs<R> a, const R* __restrict__ drho, const R* __restrict__ mubar,
-                          const R* __restrict__ rb1, R* __restrict__ lam, double* __restrict__ rows)
+                          const R* __restrict__ rb1, R* __restrict__ lam, R* __restrict__ rb_out,
+                          double* __restrict__ rows)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -284,13 +289,27 @@ __global__ void k_adj_rho(const AdjArgs<R> a, const R* __restrict__ drho, const 
         const R d = r0 + a.rho0_minus_rhoc;
         const R psi2 = a.A + R(3) * a.B * d * d;
         const R rb = rb1[s] + psi2 * mb - a.kappa * lapm;
+        if (rb_out)
+            rb_out[s] = rb;
+        else
 #pragma unroll
-        for (int i = 0; i < 19; ++i) lam[(long)i * V + s] += rb;
+            for (int i = 0; i < 19; ++i) lam[(long)i * V + s] += rb;
         gp[0] = -mb * lapr;   // kappa
         gp[1] = mb * d;       // A
         gp[2] = mb * d * d * d;  // B
     }
     block_rows<3>(gp, rows + blin() * 6 + 3);
+}
+
+// lam += rb on every population: the deferred density part of the last step
+template <class R>
+__global__ void k_add_rb(R* __restrict__ lam, const R* __restrict__ rb, long V)
+{
+    for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < V; s += (long)gridDim.x * blockDim.x) {
+        const R r = rb[s];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) lam[(long)i * V + s] += r;
+    }
 }
 
 __global__ void k_add_grads(const double* __restrict__ colsum, double* __restrict__ grad, int nonideal)
@@ -336,8 +355,9 @@ AdjArgs<R> make_adj(const HostModel& m, const Coll<R>& c)
 }
 
 template <class R>
-cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, const R* gn, const R* lam_next, R* lam,
-                           R* work, double* rows, double* colsum, double* grad, cudaStream_t st)
+cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, const R* gn, const R* lam_next,
+                           const R* rb_next, R* lam, R* rb_out, R* work, double* rows, double* colsum, double* grad,
+                           cudaStream_t st)
 {
     const long V = m.V;
     R* drho = work;
@@ -371,10 +391,10 @@ cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, 
         k_mu<L, R><<<g, b, 0, st>>>(sa, drho, mu);
         k_force<L, R><<<g, b, 0, st>>>(sa, drho, mu, F);
     }
-    k_adj_collide<R><<<g, b, 0, st>>>(a, (uint32_t)step, gn, F, lam_next, lam, Fbar, rows);
+    k_adj_collide<R><<<g, b, 0, st>>>(a, (uint32_t)step, gn, F, lam_next, rb_next, lam, Fbar, rows);
     if (m.nonideal) {
         k_adj_mu<R><<<g, b, 0, st>>>(a, drho, F, Fbar, mubar, rb1);
-        k_adj_rho<R><<<g, b, 0, st>>>(a, drho, mubar, rb1, lam, rows);
+        k_adj_rho<R><<<g, b, 0, st>>>(a, drho, mubar, rb1, lam, rb_out, rows);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if ((e = sum_columns(rows, nrows, 6, colsum, st)) != cudaSuccess) return e;
@@ -384,14 +404,27 @@ cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, 
 
 }  // namespace
 
-cudaError_t adjoint_step(const HostModel& m, int prec, uint64_t step, const void* gn, const void* lam_next, void* lam,
-                         void* work, double* rows, double* colsum, double* grad, cudaStream_t st)
+cudaError_t adjoint_step(const HostModel& m, int prec, uint64_t step, const void* gn, const void* lam_next,
+                         const void* rb_next, void* lam, void* rb_out, void* work, double* rows, double* colsum,
+                         double* grad, cudaStream_t st)
 {
     if (prec == FLB_FP64)
         return adjoint_step_t<double>(m, coll_fp64(m, step), step, (const double*)gn, (const double*)lam_next,
-                                      (double*)lam, (double*)work, rows, colsum, grad, st);
-    return adjoint_step_t<float>(m, coll_fp32(m, step), step, (const float*)gn, (const float*)lam_next, (float*)lam,
-                                 (float*)work, rows, colsum, grad, st);
+                                      (const double*)rb_next, (double*)lam, (double*)rb_out, (double*)work, rows,
+                                      colsum, grad, st);
+    return adjoint_step_t<float>(m, coll_fp32(m, step), step, (const float*)gn, (const float*)lam_next,
+                                 (const float*)rb_next, (float*)lam, (float*)rb_out, (float*)work, rows, colsum, grad,
+                                 st);
+}
+
+cudaError_t adjoint_add_rb(const HostModel& m, int prec, void* lam, const void* rb, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)std::min<long>((m.V + 255) / 256, 152 * 16);
+    if (prec == FLB_FP64)
+        k_add_rb<double><<<nb, 256, 0, st>>>((double*)lam, (const double*)rb, m.V);
+    else
+        k_add_rb<float><<<nb, 256, 0, st>>>((float*)lam, (const float*)rb, m.V);
+    return cudaGetLastError();
 }
 
 int adjoint_rows(const HostModel& m)

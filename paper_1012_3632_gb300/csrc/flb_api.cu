@@ -120,6 +120,8 @@ struct flb_ctx {
     void* adj_work = nullptr;
     double* adj_rows = nullptr;
     double* adj_col = nullptr;
+    void* adj_lam2 = nullptr;  // flb_adjoint_segment: second adjoint state (ping-pong)
+    void* adj_rb = nullptr;    // flb_adjoint_segment: deferred density parts (2 fields)
 
     // kernel timing
     bool timing = false;
@@ -173,7 +175,7 @@ int alloc_guarded(flb_ctx* c, void** p, size_t bytes, const char* name)
 void free_all(flb_ctx* c)
 {
     void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
-                    c->adj_work, c->adj_rows, c->adj_col, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
+                    c->adj_work, c->adj_rows, c->adj_col, c->adj_lam2, c->adj_rb, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
                     c->hs_tmp, c->sw_chol, c->sw_work, c->sw_xi};
     for (void* p : ptrs) {
         bool guarded = false;
@@ -876,8 +878,56 @@ int flb_adjoint_step(flb_ctx* c, const void* g_n, uint64_t step, const void* lam
         (rc = alloc((void**)&c->adj_rows, (size_t)flb::adjoint_rows(c->m) * 6 * sizeof(double))) ||
         (rc = alloc((void**)&c->adj_col, 8 * sizeof(double))))
         return rc;
-    FLB_CUDA(flb::adjoint_step(c->m, c->prec, step, g_n, lam_next, lam, c->adj_work, c->adj_rows, c->adj_col, grad,
-                               c->stream));
+    FLB_CUDA(flb::adjoint_step(c->m, c->prec, step, g_n, lam_next, nullptr, lam, nullptr, c->adj_work, c->adj_rows,
+                               c->adj_col, grad, c->stream));
+    return FLB_OK;
+}
+
+int flb_adjoint_segment(flb_ctx* c, const void* g_start, uint64_t step0, int n, void* states, void* lam,
+                        double* grad)
+{
+    FLB_TRACE();
+    if (!c || !g_start || !states || !lam || !grad) return fail(FLB_EINVAL, "NULL argument");
+    if (n < 1) return fail(FLB_EINVAL, "n must be >= 1");
+    if (c->m.Q != 19) return fail(FLB_EINVAL, "the adjoint step is implemented for D3Q19");
+    if (c->prec == FLB_BF16) return fail(FLB_EINVAL, "the adjoint step needs FLB_FP64 or FLB_FP32 storage");
+    DeviceGuard guard(c->device);
+    int rc;
+    if ((rc = alloc(&c->adj_work, 10 * c->field_bytes())) ||
+        (rc = alloc((void**)&c->adj_rows, (size_t)flb::adjoint_rows(c->m) * 6 * sizeof(double))) ||
+        (rc = alloc((void**)&c->adj_col, 8 * sizeof(double))) || (rc = alloc(&c->adj_lam2, c->pop_bytes())) ||
+        (rc = alloc(&c->adj_rb, 2 * c->field_bytes())))
+        return rc;
+    const size_t pb = c->pop_bytes();
+    char* S = (char*)states;
+    // forward: the states at step0 .. step0+n-1 (pre-collision deviations)
+    FLB_CUDA(cudaMemcpyAsync(S, g_start, pb, cudaMemcpyDeviceToDevice, c->stream));
+    FLB_CUDA(c->ops->push_state(c->m, g_start, c->buf[c->cur], c->stream));
+    c->step = step0;
+    for (int k = 1; k < n; ++k) {
+        if ((rc = flb_step(c, 1))) return rc;
+        FLB_CUDA(c->ops->pull_state(c->m, c->buf[c->cur], S + (size_t)k * pb, c->stream));
+    }
+    // reverse: lam(step0 + n) -> lam(step0), alternating between lam and
+    // adj_lam2; for the non-ideal fluid each step passes its density part on to
+    // the next (two scalars per site instead of a pass over all 19 planes) and
+    // the last one is added at the end, the same additions in the same order
+    // as flb_adjoint_step one step at a time
+    void* nxt = lam;
+    void* cur = c->adj_lam2;
+    char* rb = (char*)c->adj_rb;
+    const size_t fb = c->field_bytes();
+    const bool defer = c->m.nonideal != 0;
+    const void* rb_in = nullptr;
+    for (int k = n - 1; k >= 0; --k) {
+        void* rb_out = defer ? rb + (size_t)(k & 1) * fb : nullptr;
+        FLB_CUDA(flb::adjoint_step(c->m, c->prec, step0 + (uint64_t)k, S + (size_t)k * pb, nxt, rb_in, cur, rb_out,
+                                   c->adj_work, c->adj_rows, c->adj_col, grad, c->stream));
+        rb_in = rb_out;
+        std::swap(nxt, cur);
+    }
+    if (rb_in) FLB_CUDA(flb::adjoint_add_rb(c->m, c->prec, nxt, rb_in, c->stream));
+    if (nxt != lam) FLB_CUDA(cudaMemcpyAsync(lam, nxt, pb, cudaMemcpyDeviceToDevice, c->stream));
     return FLB_OK;
 }
 

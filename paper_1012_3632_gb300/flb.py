@@ -29,7 +29,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 EXPORTS = [
     "flb_default_options", "flb_create", "flb_init", "flb_step", "flb_moments", "flb_structure_factor",
     "flb_snapshot_count", "flb_reset_accumulators", "flb_conservation", "flb_get_populations",
-    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_z_chunk", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
+    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_z_chunk", "flb_adjoint_segment", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
     "flb_get_info", "flb_kernel_timing", "flb_kernel_times", "flb_save", "flb_load", "flb_error_string",
     "flb_last_error", "flb_destroy", "flb_structure_factor_noalloc",
     "flb_batch_create", "flb_batch_init", "flb_batch_step", "flb_batch_autotune", "flb_batch_mode_variance",
@@ -113,6 +113,7 @@ def lib():
         "flb_get_sites": (ctypes.c_int, [vp, P(ctypes.c_longlong), ctypes.c_int, dp]),
         "flb_check_guards": (ctypes.c_int, [vp]),
         "flb_z_chunk": (ctypes.c_int, [vp, ip, ip]),
+        "flb_adjoint_segment": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_int, vp, vp, vp]),
         "flb_get_step": (ctypes.c_int, [vp, P(ctypes.c_uint64)]),
         "flb_set_step": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "flb_set_stream": (ctypes.c_int, [vp, vp]),
@@ -350,6 +351,10 @@ class Context:
     def adjoint_step(self, g_n: int, step: int, lam_next: int, lam: int, grad: int):
         _check(lib().flb_adjoint_step(self._h, ctypes.c_void_p(g_n), int(step), ctypes.c_void_p(lam_next),
                                       ctypes.c_void_p(lam), ctypes.c_void_p(grad)))
+
+    def adjoint_segment(self, g_start: int, step0: int, n: int, states: int, lam: int, grad: int):
+        _check(lib().flb_adjoint_segment(self._h, ctypes.c_void_p(g_start), int(step0), int(n),
+                                         ctypes.c_void_p(states), ctypes.c_void_p(lam), ctypes.c_void_p(grad)))
 
     # -- checkpoints ---------------------------------------------------------
     def save(self, path: str):

@@ -114,3 +114,47 @@ def test_fp32_adjoint_close_to_fp64():
     l32, t32 = out["fp32"]
     assert np.allclose(t32[[0, 1, 3, 4]], t64[[0, 1, 3, 4]], rtol=2e-3)
     assert np.abs(l32 - l64).max() <= 2e-3 * np.abs(l64).max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_segment_equals_single_steps(prec):
+    """flb_adjoint_segment (recompute + reverse sweep in one call) gives bitwise
+    the lam and gradients of the same segment done with flb_step,
+    flb_get_state_device and flb_adjoint_step one step at a time."""
+    from paper_1012_3632_gb300 import Context
+    from paper_1012_3632_gb300.flb import FLBError
+
+    dims, start, n = (12, 10, 9), 5, 7
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    g0 = torch.tensor(_g0(dims, seed=4, amp=0.02), dtype=dt, device="cuda").contiguous()
+    lam0 = torch.randn(g0.shape, dtype=dt, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+    kw = dict(kT=1e-5, free_energy=FE, seed=6, precision=prec)
+    outs = []
+    with Context(19, dims, 1.1, 0.9, 1.2, **kw) as c:
+        lam, grad = lam0.clone(), torch.zeros(6, dtype=torch.float64, device="cuda")
+        states = torch.empty((n,) + tuple(g0.shape), dtype=dt, device="cuda")
+        c.adjoint_segment(g0.data_ptr(), start, n, states.data_ptr(), lam.data_ptr(), grad.data_ptr())
+        torch.cuda.synchronize()
+        outs.append((lam.cpu(), grad.cpu(), states.cpu()))
+        with pytest.raises(FLBError):
+            c.adjoint_segment(g0.data_ptr(), start, 0, states.data_ptr(), lam.data_ptr(), grad.data_ptr())
+    with Context(19, dims, 1.1, 0.9, 1.2, **kw) as c:
+        st = [g0.clone()]
+        c.set_state_device(g0.data_ptr())
+        c.step_count = start
+        for _ in range(n - 1):
+            c.step(1)
+            s = torch.empty_like(g0)
+            c.get_state_device(s.data_ptr())
+            st.append(s)
+        lam, grad = lam0.clone(), torch.zeros(6, dtype=torch.float64, device="cuda")
+        for k in reversed(range(n)):
+            nxt = torch.empty_like(lam)
+            c.adjoint_step(st[k].data_ptr(), start + k, lam.data_ptr(), nxt.data_ptr(), grad.data_ptr())
+            lam = nxt
+        torch.cuda.synchronize()
+        outs.append((lam.cpu(), grad.cpu(), torch.stack(st).cpu()))
+    (l1, g1, s1), (l2, g2, s2) = outs
+    assert torch.equal(s1, s2)
+    assert torch.equal(l1, l2)
+    assert torch.equal(g1, g2)
