@@ -34,7 +34,7 @@ def test_every_declared_symbol_is_exported(flb):
 
 def test_error_strings(flb):
     L = flb.lib()
-    for code in (0, -1, -2, -3, -4, -5, -6):
+    for code in (0, -1, -2, -3, -4, -5, -6, -7):
         assert len(L.flb_error_string(code)) > 3
     assert L.flb_error_string(-99) == b"unknown error"
 
@@ -47,6 +47,11 @@ def test_error_strings(flb):
     dict(omega_bulk=0.0),
     dict(kT=-1e-5),
     dict(kT=0.5),
+    dict(dims=(2048, 1024, 1024)),          # V = 2^31: beyond the 32-bit site index
+    dict(opts=dict(guard=2)),
+    dict(opts=dict(z_chunk=-1)),
+    dict(dims=(4, 4, 262140), opts=dict(z_chunk=1)),  # 262140 z-blocks exceed the launch grid
+    dict(opts=dict(check_every=-1)),
 ])
 def test_invalid_arguments_rejected_before_any_device_work(flb, kw):
     """flb_create validates its arguments first (FLB_EINVAL, no context)."""
@@ -55,7 +60,7 @@ def test_invalid_arguments_rejected_before_any_device_work(flb, kw):
     args.update(kw)
     h = ctypes.c_void_p()
     d = (ctypes.c_int * 3)(*args["dims"])
-    o = flb.options()
+    o = flb.options(**args.get("opts", {}))
     rc = L.flb_create(ctypes.byref(h), args["lattice"], d, args["omega_shear"], args["omega_bulk"], 1.0,
                       args["kT"], None, 1, ctypes.byref(o))
     assert rc == flb.FLB_EINVAL
@@ -66,6 +71,7 @@ def test_invalid_arguments_rejected_before_any_device_work(flb, kw):
 def test_default_options(flb):
     o = flb.options()
     assert o.precision == flb.FP32 and o.rho0 == 1.0 and o.noise_rho_local == 1 and o.device == -1
+    assert o.check_every == 0 and o.guard == 0 and o.z_chunk == 0
 
 
 def test_graft_entry_build_compiles_everything():
