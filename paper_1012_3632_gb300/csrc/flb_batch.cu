@@ -266,8 +266,6 @@ int make_graph(flb_batch* b, int p)
     return FLB_OK;
 }
 
-HostModel sub_model(const flb_batch* b, int r) { return b->m[r]; }
-
 const float* rep_src(const flb_batch* b, int r) { return b->buf[b->cur] + b->off[r]; }
 
 }  // namespace
