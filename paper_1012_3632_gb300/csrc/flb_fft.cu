@@ -145,6 +145,36 @@ __device__ __forceinline__ void butterfly(const T* __restrict__ in, T* __restric
     for (int r = 0; r < R; ++r) out[base + r * Ns] = y[r];
 }
 
+// Twiddle table tw[m] = exp(-2 pi i m / L), m < L, built by every block of
+// k_fft_lines in shared memory.  FP32 transforms: one FP32 sincospi per entry.
+// FP64 transforms: m = a S + b with S = ceil(sqrt(L)), tw[m] = coarse[a] *
+// fine[b] with coarse[a] = exp(-2 pi i a S / L), fine[b] = exp(-2 pi i b / L):
+// about 2 sqrt(L) FP64 sincospi per block instead of L (FP64 is slow on this
+// part), each entry within a few ulp.  scratch: >= S + ceil(L / S) entries.
+__device__ __forceinline__ void fill_twiddles(float2* tw, int L, float2*)
+{
+    for (int m = threadIdx.x; m < L; m += blockDim.x) {
+        float s, c;
+        sincospif(-2.0f * ((float)m / (float)L), &s, &c);
+        tw[m] = make_float2(c, s);
+    }
+}
+__device__ __forceinline__ void fill_twiddles(double2* tw, int L, double2* scratch)
+{
+    int S = 1;
+    while (S * S < L) ++S;
+    const int A = (L + S - 1) / S;
+    for (int t = threadIdx.x; t < S + A; t += blockDim.x) {
+        const int m = t < S ? t : (t - S) * S;
+        double s, c;
+        sincospi(-2.0 * (double)m / (double)L, &s, &c);
+        scratch[t] = make_double2(c, s);
+    }
+    __syncthreads();
+    for (int m = threadIdx.x; m < L; m += blockDim.x) tw[m] = cmul(scratch[S + m / S], scratch[m % S]);
+    __syncthreads();
+}
+
 template <class T>
 __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const LineGeom g, int B)
 {
@@ -155,11 +185,7 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
     T* b0 = sm;
     T* b1 = sm + (long)B * L;
     T* tw = sm + 2l * B * L;
-    for (int m = threadIdx.x; m < L; m += blockDim.x) {
-        double s, c;
-        sincospi(-2.0 * (double)m / (double)L, &s, &c);
-        tw[m] = T{E(c), E(s)};
-    }
+    fill_twiddles(tw, L, b1);  // b1 is free until the first radix pass
     const int i0 = blockIdx.x * B;
     const long o1 = (long)blockIdx.y * g.s_out;
     const int nl = min(B, g.n_in - i0);
