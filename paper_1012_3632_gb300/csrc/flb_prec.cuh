@@ -303,9 +303,11 @@ __global__ void k_force(const StepArgs<R> a, const R* __restrict__ drho, const R
     for (int d = 0; d < 3; ++d) F[d * a.V + s] = pre * gr[d] + a.pgrad * pr[d];
 }
 
-// Block sum of NV doubles per thread into out[0..NV) (one row per block).
-template <int NV>
-__device__ __forceinline__ void block_sum_row(double v[NV], double* __restrict__ row)
+// Block sum of NV values per thread into out[0..NV) (one row per block): warp
+// sums in the values' own type (32 terms; FP32 values stay off GB300's slow
+// FP64 pipe), FP64 across the warps and, in k_sum_columns, across blocks.
+template <int NV, class V>
+__device__ __forceinline__ void block_sum_row(V v[NV], double* __restrict__ row)
 {
     __shared__ double red[32][NV];
     const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
@@ -315,7 +317,7 @@ __device__ __forceinline__ void block_sum_row(double v[NV], double* __restrict__
     for (int k = 0; k < NV; ++k)
         for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
     if (lane == 0)
-        for (int k = 0; k < NV; ++k) red[warp][k] = v[k];
+        for (int k = 0; k < NV; ++k) red[warp][k] = (double)v[k];
     __syncthreads();
     const int nw = (nthr + 31) / 32;
     for (int k = tid; k < NV; k += nthr) {
@@ -337,8 +339,8 @@ __global__ void k_mode_partials(const S* __restrict__ src, double* __restrict__ 
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z * blockDim.z + threadIdx.z;
-    double v[2 * L::Q];
-    for (int q = 0; q < 2 * L::Q; ++q) v[q] = 0.0;
+    R v[2 * L::Q];
+    for (int q = 0; q < 2 * L::Q; ++q) v[q] = R(0);
     if (x < X && y < Y && z < Z) {
         const long V = (long)X * Y * Z;
         const Nbhd nb(x, y, z, X, Y, Z);
@@ -347,8 +349,8 @@ __global__ void k_mode_partials(const S* __restrict__ src, double* __restrict__ 
         L::moments(g, m);
 #pragma unroll
         for (int q = 0; q < L::Q; ++q) {
-            v[q] = (double)m[q];
-            v[L::Q + q] = (double)m[q] * (double)m[q];
+            v[q] = m[q];
+            v[L::Q + q] = m[q] * m[q];
         }
     }
     block_sum_row<2 * L::Q>(v, partials + block_linear() * (2 * L::Q));
