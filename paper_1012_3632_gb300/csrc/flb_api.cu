@@ -631,9 +631,17 @@ int flb_structure_factor(flb_ctx* c, double* S, int mode, int accumulate)
     } else {
         if ((rc = alloc((void**)&c->sk_tmp, m.V * sizeof(double)))) return rc;
     }
-    FLB_CUDA(c->ops->mode_field(m, c->buf[c->cur], mode, c->fft, c->stream));
-    FLB_CUDA(flb::fft3d(c->fft, m.X, m.Y, m.Z, c->fft_scratch, c->stream));
-    FLB_CUDA(flb::power_spectrum(c->fft, m.V, target, c->sk_tmp, c->stream));
+    // single-precision states are transformed in single precision (GB300's
+    // FP64 rate is a small fraction of its FP32 rate); |F|^2 accumulates in FP64
+    const bool fp32 = c->prec != FLB_FP64;
+    FLB_CUDA(c->ops->mode_field(m, c->buf[c->cur], mode, c->fft, fp32, c->stream));
+    if (fp32) {
+        FLB_CUDA(flb::fft3d((float2*)c->fft, m.X, m.Y, m.Z, (float2*)c->fft_scratch, c->stream));
+        FLB_CUDA(flb::power_spectrum((const float2*)c->fft, m.V, target, c->sk_tmp, c->stream));
+    } else {
+        FLB_CUDA(flb::fft3d(c->fft, m.X, m.Y, m.Z, c->fft_scratch, c->stream));
+        FLB_CUDA(flb::power_spectrum(c->fft, m.V, target, c->sk_tmp, c->stream));
+    }
     if (accumulate) c->sk_count[mode] += 1;
     if (S) {
         FLB_CUDA(cudaMemcpyAsync(S, accumulate ? c->sk_acc[mode] : c->sk_tmp, m.V * sizeof(double),

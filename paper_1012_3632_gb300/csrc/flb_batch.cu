@@ -518,7 +518,7 @@ int flb_batch_structure_factor(flb_batch* b, int replica, double* S, int mode, i
         target = slot.first;
         slot.second += 1;
     }
-    BCUDA(ops.mode_field(m, rep_src(b, replica), mode, b->fft, b->stream));
+    BCUDA(ops.mode_field(m, rep_src(b, replica), mode, b->fft, false, b->stream));
     BCUDA(flb::fft3d(b->fft, m.X, m.Y, m.Z, b->fft_scratch, b->stream));
     BCUDA(flb::power_spectrum(b->fft, m.V, target, b->sk_tmp, b->stream));
     if (S) {

@@ -351,11 +351,34 @@ __global__ void k_power(const double2* __restrict__ d, long V, double* __restric
     }
 }
 
+// |F(k)|^2 / V of a single-precision transform: the square in FP32, the
+// accumulation over snapshots in FP64.
+__global__ void k_power_sp(const float2* __restrict__ d, long V, double* __restrict__ acc, double* __restrict__ out)
+{
+    const float inv = 1.0f / (float)V;
+    for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < V; s += (long)gridDim.x * blockDim.x) {
+        const float2 v = d[s];
+        const double p = (s == 0) ? 0.0 : (double)((v.x * v.x + v.y * v.y) * inv);
+        if (acc)
+            acc[s] += p;
+        else
+            out[s] = p;
+    }
+}
+
 cudaError_t power_spectrum(const double2* data, long V, double* acc, double* out, cudaStream_t s)
 {
     long nb = (V + 255) / 256;
     if (nb > 152 * 32) nb = 152 * 32;
     k_power<<<(unsigned)nb, 256, 0, s>>>(data, V, acc, out);
+    return cudaGetLastError();
+}
+
+cudaError_t power_spectrum(const float2* data, long V, double* acc, double* out, cudaStream_t s)
+{
+    long nb = (V + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_power_sp<<<(unsigned)nb, 256, 0, s>>>(data, V, acc, out);
     return cudaGetLastError();
 }
 

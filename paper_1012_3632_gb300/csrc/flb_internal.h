@@ -68,7 +68,9 @@ struct PrecOps {
                                  cudaStream_t);
     cudaError_t (*cons_partials)(const HostModel&, const void* src, double* partials, int* nrows,
                                  cudaStream_t);
-    cudaError_t (*mode_field)(const HostModel&, const void* src, int mode, double2* out, cudaStream_t);
+    // mode a of the pre-collision state as a complex field: double2, or float2
+    // when fp32 (the transform of single-precision states)
+    cudaError_t (*mode_field)(const HostModel&, const void* src, int mode, void* out, bool fp32, cudaStream_t);
     int (*partial_rows_max)(const HostModel&);
     int (*step_needs_density)(const HostModel&);
     // pre-collision deviations in the storage type, [i][s], to / from a device buffer
@@ -137,5 +139,6 @@ int adjoint_rows(const HostModel& m);
 
 // p = |data|^2 / V with p(0) = 0; accumulate: acc += p, else out = p.
 cudaError_t power_spectrum(const double2* data, long V, double* acc, double* out, cudaStream_t s);
+cudaError_t power_spectrum(const float2* data, long V, double* acc, double* out, cudaStream_t s);
 
 }  // namespace flb

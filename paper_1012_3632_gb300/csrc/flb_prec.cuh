@@ -424,8 +424,8 @@ inline int cons_blocks(long V)
     return (int)std::min<long>((V + kConsThreads - 1) / kConsThreads, kConsBlocksMax);
 }
 
-template <class L, class R, class S>
-__global__ void k_mode_field(const S* __restrict__ src, int mode, double2* __restrict__ out, int X, int Y, int Z)
+template <class L, class R, class S, class T>
+__global__ void k_mode_field(const S* __restrict__ src, int mode, T* __restrict__ out, int X, int Y, int Z)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -440,7 +440,8 @@ __global__ void k_mode_field(const S* __restrict__ src, int mode, double2* __res
 #pragma unroll
     for (int q = 1; q < L::Q; ++q)
         if (q == mode) v = m[q];
-    out[x + X * (y + Y * z)] = make_double2((double)v, 0.0);
+    using E = decltype(T::x);
+    out[x + X * (y + Y * z)] = T{E(v), E(0)};
 }
 
 // ---------------------------------------------------------------------------
@@ -652,16 +653,21 @@ struct Prec {
         }
         return cudaGetLastError();
     }
-    static cudaError_t mode_field(const HostModel& m, const void* src, int mode, double2* out, cudaStream_t st)
+    template <class T>
+    static cudaError_t mode_field_t(const HostModel& m, const void* src, int mode, T* out, cudaStream_t st)
     {
         if (m.Q == 19) {
             const dim3 b = site_block<D3Q19>();
-            k_mode_field<D3Q19, R, S><<<grid_for(m, b), b, 0, st>>>((const S*)src, mode, out, m.X, m.Y, m.Z);
+            k_mode_field<D3Q19, R, S, T><<<grid_for(m, b), b, 0, st>>>((const S*)src, mode, out, m.X, m.Y, m.Z);
         } else {
             const dim3 b = site_block<D2Q9>();
-            k_mode_field<D2Q9, R, S><<<grid_for(m, b), b, 0, st>>>((const S*)src, mode, out, m.X, m.Y, m.Z);
+            k_mode_field<D2Q9, R, S, T><<<grid_for(m, b), b, 0, st>>>((const S*)src, mode, out, m.X, m.Y, m.Z);
         }
         return cudaGetLastError();
+    }
+    static cudaError_t mode_field(const HostModel& m, const void* src, int mode, void* out, bool fp32, cudaStream_t st)
+    {
+        return fp32 ? mode_field_t(m, src, mode, (float2*)out, st) : mode_field_t(m, src, mode, (double2*)out, st);
     }
 
     static cudaError_t pull_state(const HostModel& m, const void* src, void* out, cudaStream_t st)

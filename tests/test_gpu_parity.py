@@ -191,6 +191,25 @@ def test_structure_factor(dims):
         assert np.allclose(mean, 0.5 * (s1 + s2), rtol=1e-12, atol=1e-20)
 
 
+@pytest.mark.parametrize("Q,dims,prec", [(19, (12, 10, 9), "fp32"), (19, (16, 15, 8), "bf16"), (9, (20, 14, 1), "fp32"),
+                                         (19, (14, 6, 5), "fp32")])
+def test_structure_factor_single_precision_state(Q, dims, prec):
+    """FP32 and BF16 states are transformed with the FP32 FFT (|F|^2 summed in
+    FP64): S_a(k) of the GPU's own state against the oracle's FP64 DFT of the
+    same populations, within the FP32 transform's rounding (14 = 2 * 7 takes
+    the direct DFT)."""
+    kw = dict(kT=1e-4, omega_shear=1.2, seed=6)
+    ctx, p = _pair(Q, dims, prec, **kw)
+    with ctx:
+        ctx.init(thermal=True)
+        ctx.step(3)
+        f = ctx.get_populations()
+        for mode in (0, 1, Q - 1):
+            S = ctx.structure_factor(mode)
+            want = oracle.structure_factor(p, f, mode)
+            assert np.allclose(S, want, rtol=1e-4, atol=1e-5 * want.max()), mode
+
+
 def test_mode_variance_accumulator():
     Q, dims = 19, (8, 7, 6)
     kw = dict(kT=1e-4, omega_shear=1.2, seed=6)
