@@ -78,10 +78,10 @@ WORKLOADS = {
 # Algorithmic bytes per site and step of the path: every population is pulled
 # (read) and stored once, and the non-ideal fluid also reads every population
 # once more for the density gather, writes the density and reads it back (Q e +
-# 2 e_rho).  The D3Q19 non-ideal kernel does all of this in one launch and takes
-# the gather's re-reads and the density from L2 and shared memory, so its DRAM
-# minimum is that of the ideal step (2 Q e); the D2Q9 non-ideal step reads a
-# density field written by a separate gather kernel.
+# 2 e_rho).  The force-model steps (D3Q19 and D2Q9) do all of this in one launch
+# and take the gather's re-reads and the density from L2 and shared memory, so
+# their DRAM minimum is that of the ideal step (2 Q e); the modified-equilibrium
+# step reads a density field and a noise field written before it.
 ELEM = {"fp32": 4, "fp64": 8, "bf16": 2}
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -99,8 +99,6 @@ def step_bytes(wl):
     if wl["fe"].get("model", 0) == 1:  # + the density and the coloured e/eps noise field
         nf = 16 if wl["precision"] == "fp64" else 8
         return 2 * Q * e + rb + nf, Q * e + rb, 2 * Q * e + rb + nf
-    if Q == 9:
-        return 2 * Q * e + rb, Q * e + rb, 2 * Q * e + rb
     return 3 * Q * e + 2 * rb, 0, 2 * Q * e
 
 

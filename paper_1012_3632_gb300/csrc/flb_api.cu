@@ -644,13 +644,15 @@ int flb_structure_factor(flb_ctx* c, double* S, int mode, int accumulate)
     }
     if (accumulate) c->sk_count[mode] += 1;
     if (S) {
-        FLB_CUDA(cudaMemcpyAsync(S, accumulate ? c->sk_acc[mode] : c->sk_tmp, m.V * sizeof(double),
-                                 cudaMemcpyDeviceToHost, c->stream));
-        FLB_CUDA(cudaStreamSynchronize(c->stream));
+        const double* src = c->sk_tmp;
         if (accumulate) {
-            const double inv = 1.0 / c->sk_count[mode];
-            for (long s = 0; s < m.V; ++s) S[s] *= inv;
+            // the mean over the snapshots, formed on the device
+            if ((rc = alloc((void**)&c->sk_tmp, m.V * sizeof(double)))) return rc;
+            FLB_CUDA(flb::scale_copy(c->sk_acc[mode], 1.0 / c->sk_count[mode], m.V, c->sk_tmp, c->stream));
+            src = c->sk_tmp;
         }
+        FLB_CUDA(cudaMemcpyAsync(S, src, m.V * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        FLB_CUDA(cudaStreamSynchronize(c->stream));
     }
     return FLB_OK;
 }

@@ -374,6 +374,20 @@ cudaError_t power_spectrum(const double2* data, long V, double* acc, double* out
     return cudaGetLastError();
 }
 
+__global__ void k_scale_copy(const double* __restrict__ in, double a, long V, double* __restrict__ out)
+{
+    for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < V; s += (long)gridDim.x * blockDim.x)
+        out[s] = a * in[s];
+}
+
+cudaError_t scale_copy(const double* in, double a, long V, double* out, cudaStream_t s)
+{
+    long nb = (V + 255) / 256;
+    if (nb > 152 * 32) nb = 152 * 32;
+    k_scale_copy<<<(unsigned)nb, 256, 0, s>>>(in, a, V, out);
+    return cudaGetLastError();
+}
+
 cudaError_t power_spectrum(const float2* data, long V, double* acc, double* out, cudaStream_t s)
 {
     long nb = (V + 255) / 256;

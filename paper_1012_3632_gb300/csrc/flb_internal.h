@@ -140,5 +140,7 @@ int adjoint_rows(const HostModel& m);
 // p = |data|^2 / V with p(0) = 0; accumulate: acc += p, else out = p.
 cudaError_t power_spectrum(const double2* data, long V, double* acc, double* out, cudaStream_t s);
 cudaError_t power_spectrum(const float2* data, long V, double* acc, double* out, cudaStream_t s);
+// out[s] = a * in[s], s < V
+cudaError_t scale_copy(const double* in, double a, long V, double* out, cudaStream_t s);
 
 }  // namespace flb

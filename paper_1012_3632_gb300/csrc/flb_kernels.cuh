@@ -248,9 +248,12 @@ __global__ void k_density(const S* __restrict__ src, R* __restrict__ drho, int X
 
 // ---------------------------------------------------------------------------
 // Fused pull + collide (+ force) + store.  Block = TX*TY*TZ threads, one site
-// each.  NONIDEAL adds the shared-memory mu / F stencils.
+// each.  NONIDEAL adds the shared-memory mu / F stencils; their density tile
+// (tile + 2-site halo) comes from the field drho, or with GATHER from the
+// populations themselves (each halo site's pulls summed as k_density does),
+// which saves the separate density launch and field.
 // ---------------------------------------------------------------------------
-template <class L, class R, class S, bool NONIDEAL, int TX, int TY, int TZ>
+template <class L, class R, class S, bool NONIDEAL, int TX, int TY, int TZ, bool GATHER = false>
 __global__ void __launch_bounds__(TX* TY* TZ)
     k_step(const StepArgs<R> a, const __grid_constant__ Planes<S> P, const R* __restrict__ drho)
 {
@@ -272,7 +275,17 @@ __global__ void __launch_bounds__(TX* TY* TZ)
         for (int e = tid; e < RZ * RY * RX; e += NT) {
             const int lx = e % RX, ly = (e / RX) % RY, lz = e / (RX * RY);
             const int gx = wrap_any(x0 + lx, X), gy = wrap_any(y0 + ly, Y), gz = wrap_any(z0 + lz, Z);
-            srho[e] = drho[gx + (long)X * (gy + (long)Y * gz)];
+            if constexpr (GATHER) {
+                const Nbhd nh(gx, gy, gz, X, Y, Z);
+                R g[L::Q], m[L::Q];
+#pragma unroll
+                for (int i = 0; i < L::Q; ++i)
+                    g[i] = load_s<R>(P.src[i] + nh.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i)));
+                L::moments(g, m);
+                srho[e] = m[0];
+            } else {
+                srho[e] = drho[gx + (long)X * (gy + (long)Y * gz)];
+            }
         }
         __syncthreads();
         // mu = psi'(rho) - kappa lap rho on the tile + 1 halo;

@@ -474,14 +474,14 @@ struct Prec {
         return m.Q == 19 ? density_l<D3Q19>(m, pop, drho, st) : density_l<D2Q9>(m, pop, drho, st);
     }
 
-    template <class L, bool NI, int TX, int TY, int TZ>
+    template <class L, bool NI, int TX, int TY, int TZ, bool GATHER = false>
     static cudaError_t step_t(const HostModel& m, uint64_t step, const void* src, void* dst, const void* drho,
                               cudaStream_t st)
     {
         const StepArgs<R> a = make_args<L, R>(m, step);
         const dim3 b(TX, TY, TZ);
-        k_step<L, R, S, NI, TX, TY, TZ><<<grid_for(m, b), b, 0, st>>>(a, make_planes<S>(src, dst, L::Q, m.V),
-                                                                       (const R*)drho);
+        k_step<L, R, S, NI, TX, TY, TZ, GATHER><<<grid_for(m, b), b, 0, st>>>(
+            a, make_planes<S>(src, dst, L::Q, m.V), (const R*)drho);
         return cudaGetLastError();
     }
     static cudaError_t step(const HostModel& m, uint64_t t, const void* src, void* dst, const void* drho,
@@ -535,7 +535,8 @@ struct Prec {
             }
             return step_t<D3Q19, false, 32, 4, 2>(m, t, src, dst, drho, st);
         }
-        if (m.nonideal) return step_t<D2Q9, true, 32, 8, 1>(m, t, src, dst, drho, st);
+        // force model: the density tile is gathered inside the step
+        if (m.nonideal) return step_t<D2Q9, true, 32, 8, 1, true>(m, t, src, dst, drho, st);
         return step_t<D2Q9, false, 32, 8, 1>(m, t, src, dst, drho, st);
     }
 
@@ -607,11 +608,9 @@ struct Prec {
     }
     // The D2Q9 non-ideal step reads a density field gathered beforehand; the
     // D3Q19 one gathers the density itself.
-    static int needs_density(const HostModel& m)
-    {
-        if (!m.nonideal) return 0;
-        return m.Q == 9 ? 1 : 0;
-    }
+    // a density field written before the step: only the modified-equilibrium
+    // step reads one (the force-model steps gather their density themselves)
+    static int needs_density(const HostModel& m) { return m.nonideal && m.Q == 9 && m.model == 1 ? 1 : 0; }
     static int rows(const HostModel& m)
     {
         const dim3 b = m.Q == 19 ? site_block<D3Q19>() : site_block<D2Q9>();

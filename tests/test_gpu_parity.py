@@ -245,10 +245,16 @@ def test_checkpoint_resume_is_bitwise(tmp_path, prec):
     assert np.array_equal(fa, fb)
 
 
-@pytest.mark.parametrize("Q,dims,gathers", [(19, (32, 16, 8), 0), (9, (32, 16, 1), 5)])
-def test_kernel_timing_counts_launches(Q, dims, gathers):
-    """D3Q19 gathers the density inside the fused kernel; D2Q9 runs a gather kernel first."""
-    with Context(Q, dims, precision="fp32", free_energy=FE, kT=1e-6, omega_shear=1.0) as ctx:
+SWIFT_FE = dict(A=-0.025, B=0.4, rho_c=0.75, kappa=0.08, total=True, model=1)
+
+
+@pytest.mark.parametrize("Q,dims,fe,gathers", [(19, (32, 16, 8), FE, 0), (9, (32, 16, 1), FE, 0),
+                                               (9, (32, 16, 1), SWIFT_FE, 5)])
+def test_kernel_timing_counts_launches(Q, dims, fe, gathers):
+    """The force-model steps gather the density inside the step kernel; the
+    modified-equilibrium step reads a density field (and its coloured noise)
+    made by a launch before it."""
+    with Context(Q, dims, precision="fp32", free_energy=fe, kT=1e-6, omega_shear=1.0) as ctx:
         ctx.init(rho=inputs.uniform_density(dims))
         ctx.kernel_timing(True)
         ctx.step(5)
