@@ -35,16 +35,17 @@ namespace flb {
 namespace {
 
 // Z(r) = z_e(r) + i z_eps(r): normals 0 and 5 of the D2Q9 collision draw
-// (calls 0 and 1 of tag 0), in FP64, stored as T (double2 or float2).
+// (calls 0 and 1 of tag 0), stored as T: Box-Muller in FP64 for double2 and in
+// FP32 for float2, as the collision kernels of those precisions draw them.
 template <class T>
 __global__ void k_swift_white(PhiloxKeys key, uint32_t step, uint32_t replica, long V, T* __restrict__ Z)
 {
     using E = decltype(T::x);
     for (long s = blockIdx.x * (long)blockDim.x + threadIdx.x; s < V; s += (long)gridDim.x * blockDim.x) {
-        double a[4], b[4];
-        normals4<double>(key, (uint32_t)s, step, 0u, replica, a);
-        normals4<double>(key, (uint32_t)s, step, 1u, replica, b);
-        Z[s] = T{E(a[0]), E(b[1])};
+        E a[4], b[4];
+        normals4<E>(key, (uint32_t)s, step, 0u, replica, a);
+        normals4<E>(key, (uint32_t)s, step, 1u, replica, b);
+        Z[s] = T{a[0], b[1]};
     }
 }
 
