@@ -518,17 +518,15 @@ int flb_batch_structure_factor(flb_batch* b, int replica, double* S, int mode, i
         target = slot.first;
         slot.second += 1;
     }
-    BCUDA(ops.mode_field(m, rep_src(b, replica), mode, b->fft, false, b->stream));
-    BCUDA(flb::fft3d(b->fft, m.X, m.Y, m.Z, b->fft_scratch, b->stream));
-    BCUDA(flb::power_spectrum(b->fft, m.V, target, b->sk_tmp, b->stream));
+    // FP32 states: FP32 transform, |F|^2 summed in FP64 (as flb_structure_factor)
+    BCUDA(ops.mode_field(m, rep_src(b, replica), mode, b->fft, true, b->stream));
+    BCUDA(flb::fft3d((float2*)b->fft, m.X, m.Y, m.Z, (float2*)b->fft_scratch, b->stream));
+    BCUDA(flb::power_spectrum((const float2*)b->fft, m.V, target, b->sk_tmp, b->stream));
     if (S) {
-        BCUDA(cudaMemcpyAsync(S, accumulate ? target : b->sk_tmp, m.V * sizeof(double), cudaMemcpyDeviceToHost,
-                              b->stream));
+        if (accumulate)
+            BCUDA(flb::scale_copy(target, 1.0 / b->sk_acc[{replica, mode}].second, m.V, b->sk_tmp, b->stream));
+        BCUDA(cudaMemcpyAsync(S, b->sk_tmp, m.V * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
         BCUDA(cudaStreamSynchronize(b->stream));
-        if (accumulate) {
-            const double inv = 1.0 / b->sk_acc[{replica, mode}].second;
-            for (long s = 0; s < m.V; ++s) S[s] *= inv;
-        }
     }
     return FLB_OK;
 }

@@ -81,3 +81,24 @@ def test_ensemble_mode_temperatures():
     V = np.array([np.prod(d) for d in dims])
     T[:, :4] *= (V / (V - 1.0))[:, None]  # the site mean removes k = 0 of the conserved modes
     assert np.all(np.abs(T.mean(axis=0) - 1) < 0.02), T.mean(axis=0)
+
+
+def test_batch_structure_factor_matches_oracle():
+    """flb_batch_structure_factor of each replica (FP32 transform, |F|^2 summed in
+    FP64) against the oracle's FP64 DFT of the replica's populations; the
+    accumulated mean of two snapshots is their average."""
+    with Batch(DIMS, OMS, KTS, SEEDS, omega_bulk=OMB, omega_ghost=OMG) as b:
+        b.init(thermal=True)
+        b.step(4)
+        for r, dims in enumerate(DIMS):
+            f = b.get_populations(r)
+            p = oracle.Params(Q=19, dims=dims, replica=r, omega_shear=OMS[r], kT=KTS[r], seed=SEEDS[r])
+            for mode in (0, 3, 18):
+                S = b.structure_factor(r, mode)
+                want = oracle.structure_factor(p, f, mode)
+                assert np.allclose(S, want, rtol=1e-4, atol=1e-5 * want.max()), (r, mode)
+        s1 = b.structure_factor(1, 0, accumulate=True)
+        b.step(3)
+        s2 = b.structure_factor(1, 0)
+        mean = b.structure_factor(1, 0, accumulate=True)
+        assert np.allclose(mean, 0.5 * (s1 + s2), rtol=1e-12, atol=1e-20)
