@@ -145,6 +145,42 @@ __device__ __forceinline__ void butterfly(const T* __restrict__ in, T* __restric
     for (int r = 0; r < R; ++r) out[base + r * Ns] = y[r];
 }
 
+// The same pass for a power-of-two line (radices 4 and 2 only): the index
+// arithmetic by shifts and masks instead of integer division (lgL = log2 L,
+// lgNs = log2 Ns).
+template <int R, class T>
+__device__ __forceinline__ void butterfly_p2(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tw,
+                                             int lgL, int lgNs, int j)
+{
+    constexpr int lgR = R == 2 ? 1 : 2;
+    const int stride = 1 << (lgL - lgR);
+    const int k = j & ((1 << lgNs) - 1);
+    T v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
+    if (lgNs > 0) {
+        const int step = k << (lgL - lgNs - lgR);  // k L / (Ns R)
+        const int mask = (1 << lgL) - 1;
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[(r * step) & mask]);
+    }
+    T y[R];
+    if constexpr (R == 2) {
+        y[0] = cadd(v[0], v[1]);
+        y[1] = csub(v[0], v[1]);
+    } else {
+        const T a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+        const T c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+        y[0] = cadd(a, c);
+        y[2] = csub(a, c);
+        y[1] = T{b.x + d.y, b.y - d.x};  // b - i d
+        y[3] = T{b.x - d.y, b.y + d.x};  // b + i d
+    }
+    const int base = ((j >> lgNs) << (lgNs + lgR)) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[base + (r << lgNs)] = y[r];
+}
+
 // Twiddle table tw[m] = exp(-2 pi i m / L), m < L, built by every block of
 // k_fft_lines in shared memory.  FP32 transforms: one FP32 sincospi per entry.
 // FP64 transforms: m = a S + b with S = ceil(sqrt(L)), tw[m] = coarse[a] *
@@ -190,14 +226,17 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
     const long o1 = (long)blockIdx.y * g.s_out;
     const int nl = min(B, g.n_in - i0);
     const int tot = nl * L;
+    // power-of-two lines (and line counts): shifts and masks for the indices
+    const bool p2 = (L & (L - 1)) == 0, nl2 = (nl & (nl - 1)) == 0;
+    const int lgL = __ffs(L) - 1, lgnl = __ffs(nl) - 1;
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
         int l, j;
         if (g.es == 1) {
-            l = e / L;
-            j = e % L;
+            l = p2 ? e >> lgL : e / L;
+            j = p2 ? e & (L - 1) : e % L;
         } else {
-            l = e % nl;
-            j = e / nl;
+            l = nl2 ? e & (nl - 1) : e % nl;
+            j = nl2 ? e >> lgnl : e / nl;
         }
         b0[l * L + j] = data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es];
     }
@@ -205,7 +244,26 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
     int Ns = 1;
     T* cur = b0;
     T* nxt = b1;
-    for (int p = 0; p < plan.nrad; ++p) {
+    if (p2) {
+        int lgNs = 0;
+        for (int p = 0; p < plan.nrad; ++p) {
+            const int lgR = plan.rad[p] == 4 ? 2 : 1;
+            const int lgper = lgL - lgR;
+            for (int t = threadIdx.x; t < (nl << lgper); t += blockDim.x) {
+                const int l = t >> lgper, j = t & ((1 << lgper) - 1);
+                if (lgR == 2)
+                    butterfly_p2<4>(cur + (l << lgL), nxt + (l << lgL), tw, lgL, lgNs, j);
+                else
+                    butterfly_p2<2>(cur + (l << lgL), nxt + (l << lgL), tw, lgL, lgNs, j);
+            }
+            __syncthreads();
+            lgNs += lgR;
+            T* tmp = cur;
+            cur = nxt;
+            nxt = tmp;
+        }
+    }
+    for (int p = 0; p < (p2 ? 0 : plan.nrad); ++p) {
         const int R = plan.rad[p];
         const int per = L / R;
         for (int t = threadIdx.x; t < nl * per; t += blockDim.x) {
@@ -226,11 +284,11 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
     for (int e = threadIdx.x; e < tot; e += blockDim.x) {
         int l, j;
         if (g.es == 1) {
-            l = e / L;
-            j = e % L;
+            l = p2 ? e >> lgL : e / L;
+            j = p2 ? e & (L - 1) : e % L;
         } else {
-            l = e % nl;
-            j = e / nl;
+            l = nl2 ? e & (nl - 1) : e % nl;
+            j = nl2 ? e >> lgnl : e / nl;
         }
         data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es] = cur[l * L + j];
     }
