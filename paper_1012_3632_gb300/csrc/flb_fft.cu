@@ -147,17 +147,22 @@ __device__ __forceinline__ void butterfly(const T* __restrict__ in, T* __restric
 
 // The same pass for a power-of-two line (radices 4 and 2 only): the index
 // arithmetic by shifts and masks instead of integer division (lgL = log2 L,
-// lgNs = log2 Ns).
+// lgNs = log2 Ns), o = the line's first element, buffers padded by pad16.
+// Shared-memory line buffers of the power-of-two path skip one element after
+// every 16 (an 8- or 16-byte element spans 2 or 4 banks), which spreads the
+// strided accesses of the early passes over the banks.
+__device__ __forceinline__ int pad16(int i) { return i + (i >> 4); }
+
 template <int R, class T>
 __device__ __forceinline__ void butterfly_p2(const T* __restrict__ in, T* __restrict__ out, const T* __restrict__ tw,
-                                             int lgL, int lgNs, int j)
+                                             int lgL, int lgNs, int j, int o)
 {
     constexpr int lgR = R == 2 ? 1 : 2;
     const int stride = 1 << (lgL - lgR);
     const int k = j & ((1 << lgNs) - 1);
     T v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = in[j + r * stride];
+    for (int r = 0; r < R; ++r) v[r] = in[pad16(o + j + r * stride)];
     if (lgNs > 0) {
         const int step = k << (lgL - lgNs - lgR);  // k L / (Ns R)
         const int mask = (1 << lgL) - 1;
@@ -176,9 +181,9 @@ __device__ __forceinline__ void butterfly_p2(const T* __restrict__ in, T* __rest
         y[1] = T{b.x + d.y, b.y - d.x};  // b - i d
         y[3] = T{b.x - d.y, b.y + d.x};  // b + i d
     }
-    const int base = ((j >> lgNs) << (lgNs + lgR)) + k;
+    const int base = o + ((j >> lgNs) << (lgNs + lgR)) + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) out[base + (r << lgNs)] = y[r];
+    for (int r = 0; r < R; ++r) out[pad16(base + (r << lgNs))] = y[r];
 }
 
 // Twiddle table tw[m] = exp(-2 pi i m / L), m < L, built by every block of
@@ -218,9 +223,10 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
     extern __shared__ __align__(16) unsigned char smraw[];
     T* sm = reinterpret_cast<T*>(smraw);
     const int L = g.L;
+    const int BLp = B * L + ((B * L) >> 4) + 1;  // a line buffer, room for the pad16 layout
     T* b0 = sm;
-    T* b1 = sm + (long)B * L;
-    T* tw = sm + 2l * B * L;
+    T* b1 = sm + BLp;
+    T* tw = sm + 2 * BLp;
     fill_twiddles(tw, L, b1);  // b1 is free until the first radix pass
     const int i0 = blockIdx.x * B;
     const long o1 = (long)blockIdx.y * g.s_out;
@@ -238,7 +244,7 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
             l = nl2 ? e & (nl - 1) : e % nl;
             j = nl2 ? e >> lgnl : e / nl;
         }
-        b0[l * L + j] = data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es];
+        b0[p2 ? pad16(l * L + j) : l * L + j] = data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es];
     }
     __syncthreads();
     int Ns = 1;
@@ -252,9 +258,9 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
             for (int t = threadIdx.x; t < (nl << lgper); t += blockDim.x) {
                 const int l = t >> lgper, j = t & ((1 << lgper) - 1);
                 if (lgR == 2)
-                    butterfly_p2<4>(cur + (l << lgL), nxt + (l << lgL), tw, lgL, lgNs, j);
+                    butterfly_p2<4>(cur, nxt, tw, lgL, lgNs, j, l << lgL);
                 else
-                    butterfly_p2<2>(cur + (l << lgL), nxt + (l << lgL), tw, lgL, lgNs, j);
+                    butterfly_p2<2>(cur, nxt, tw, lgL, lgNs, j, l << lgL);
             }
             __syncthreads();
             lgNs += lgR;
@@ -290,7 +296,7 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
             l = nl2 ? e & (nl - 1) : e % nl;
             j = nl2 ? e >> lgnl : e / nl;
         }
-        data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es] = cur[l * L + j];
+        data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es] = cur[p2 ? pad16(l * L + j) : l * L + j];
     }
 }
 
@@ -341,7 +347,7 @@ static cudaError_t fft_smem_optin()
     std::lock_guard<std::mutex> lock(mtx);
     if (!done[dev]) {
         e = cudaFuncSetAttribute(k_fft_lines<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((2 * 4096 + 4096) * sizeof(T)));
+                                 (int)((2 * (4096 + 256 + 1) + 4096) * sizeof(T)));
         if (e != cudaSuccess) return e;
         done[dev] = true;
     }
@@ -357,7 +363,7 @@ static cudaError_t fft_axis(T* data, T* scratch, int L, long es, long s_in, int 
     const LineGeom g{L, es, s_in, s_out, n_in};
     if (L <= 4096 && make_plan(L, plan)) {
         const int B = L >= 2048 ? 1 : (2048 / L < 16 ? 2048 / L : 16);
-        const size_t smem = (2ull * B * L + L) * sizeof(T);
+        const size_t smem = (2ull * (B * L + ((B * L) >> 4) + 1) + L) * sizeof(T);
         cudaError_t e = fft_smem_optin<T>();
         if (e != cudaSuccess) return e;
         const dim3 grid((n_in + B - 1) / B, n_out);
