@@ -539,8 +539,8 @@ def main():
 
     # ---- end to end through the C ABI with host buffers ---------------------
     # the initial density field (pinned host -> device) in; every step
-    # flb_step and the step's result, the FP64 mass and momentum sums
-    # (flb_conservation, 32 bytes device -> host); the density field out.
+    # flb_step_sums: the step and its result, the FP64 mass and momentum sums of
+    # the state it starts from (32 bytes device -> host); the density field out.
     host_in = torch.empty(V, dtype=torch.float64, pin_memory=True).numpy()
     host_out = torch.empty(V, dtype=torch.float64, pin_memory=True).numpy()
     host_in[:] = rho if rho is not None else 1.0
@@ -553,8 +553,7 @@ def main():
         ctx.init(rho=host_in, u=u, thermal=True)
     sums = np.empty((args.steps, 4))
     for t in range(args.steps):
-        ctx.step(1)
-        sums[t] = ctx.conservation()
+        ctx.step_sums(1, out=sums[t:t + 1])
     ctx.moments(RHO, out=host_out)
     torch.cuda.synchronize()
     t_e2e = time.perf_counter() - t0
@@ -562,8 +561,9 @@ def main():
     bytes_u = 0 if wl["fe"] else 3 * V * 8
     e2e = {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": (V * 8 + bytes_u) / args.steps,
            "d2h_bytes_per_step": 32 + V * 8 / args.steps,
-           "what": "flb_init from a pinned host density field; per step flb_step + flb_conservation (FP64 mass "
-                   "and momentum to the host); flb_moments(RHO) to pinned host at the end",
+           "what": "flb_init from a pinned host density field; per step flb_step_sums (the step, and the FP64 mass "
+                   "and momentum of the state it starts from read back to the host); flb_moments(RHO) to pinned "
+                   "host at the end",
            "mass_drift": float(abs(sums[-1, 0] - sums[0, 0]) / abs(sums[0, 0]))}
 
     ctx.close()

@@ -249,6 +249,17 @@ int flb_z_chunk(flb_ctx* ctx, int* planes, int* tuning);
  * buffer are not detected. */
 int flb_check_guards(flb_ctx* ctx);
 
+/* flb_step(ctx, nsteps) that also reports, for every step, the total mass and
+ * momentum of the state the step starts from: sums[4*t + 0] = sum rho,
+ * sums[4*t + 1..3] = sum_r sum_i f_i c_i (as flb_conservation), t < nsteps.
+ * sums: host, 4*nsteps doubles, written when the call returns (it waits for
+ * the context's stream once, at the end).  The D3Q19 force-model step with
+ * FP32 or BF16 storage and even X forms these sums inside the step kernel
+ * (per-block partial sums of the density it holds and of the populations it
+ * pulls); every other step runs the reduction of flb_conservation before the
+ * step.  Errors as flb_step. */
+int flb_step_sums(flb_ctx* ctx, int nsteps, double* sums);
+
 /* Total mass and momentum of the current state, summed on the GPU in double:
  * out[0] = sum rho, out[1..3] = sum_r sum_i f_i c_i (z component 0 for D2Q9). */
 int flb_conservation(flb_ctx* ctx, double out[4]);

@@ -122,6 +122,8 @@ struct flb_ctx {
     double* adj_col = nullptr;
     void* adj_lam2 = nullptr;  // flb_adjoint_segment: second adjoint state (ping-pong)
     void* adj_rb = nullptr;    // flb_adjoint_segment: deferred density parts (2 fields)
+    double* ss_dev = nullptr;  // flb_step_sums: 4 sums per step (device)
+    size_t ss_cap = 0;
 
     // kernel timing
     bool timing = false;
@@ -175,7 +177,7 @@ int alloc_guarded(flb_ctx* c, void** p, size_t bytes, const char* name)
 void free_all(flb_ctx* c)
 {
     void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
-                    c->adj_work, c->adj_rows, c->adj_col, c->adj_lam2, c->adj_rb, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
+                    c->adj_work, c->adj_rows, c->adj_col, c->adj_lam2, c->adj_rb, c->ss_dev, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
                     c->hs_tmp, c->sw_chol, c->sw_work, c->sw_xi};
     for (void* p : ptrs) {
         bool guarded = false;
@@ -510,12 +512,12 @@ int flb_init(flb_ctx* c, const double* rho, const double* u, int thermal_init)
     return flb_reset_accumulators(c);
 }
 
-int flb_step(flb_ctx* c, int nsteps)
+// The time steps of flb_step; with dev_sums (device, 4 doubles per step) also
+// the sums of the state each step starts from: the step kernel's own partial
+// sums where it provides them, else the conservation reduction before the step.
+// dev_sums[0] holds the mass deviation (the caller adds rho0 V).
+static int step_impl(flb_ctx* c, int nsteps, double* dev_sums)
 {
-    FLB_TRACE();
-    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
-    if (nsteps < 0) return fail(FLB_EINVAL, "nsteps must be >= 0");
-    DeviceGuard guard(c->device);
     for (int t = 0; t < nsteps; ++t) {
         const void* src = c->buf[c->cur];
         void* dst = c->buf[c->cur ^ 1];
@@ -537,7 +539,21 @@ int flb_step(flb_ctx* c, int nsteps)
             c->m.zchunk = c->zt.cand[c->zt.issued % c->zt.cand.size()];
             FLB_CUDA(cudaEventRecord(c->zt.ev[2 * c->zt.issued], c->stream));
         }
-        const cudaError_t se = c->ops->step(c->m, c->step, src, dst, c->drho, c->stream);
+        cudaError_t se;
+        if (dev_sums) {
+            int nrows = 0;
+            se = c->ops->step_rows(c->m, c->step, src, dst, c->drho, c->partials, &nrows, c->stream);
+            if (se == cudaErrorNotSupported) {
+                // this step kernel has no partial sums: reduce the state first
+                FLB_CUDA(c->ops->cons_partials(c->m, src, c->partials, &nrows, c->stream));
+                FLB_CUDA(flb::sum_columns(c->partials, nrows, 4, dev_sums + 4 * (size_t)t, c->stream));
+                se = c->ops->step(c->m, c->step, src, dst, c->drho, c->stream);
+            } else if (se == cudaSuccess) {
+                se = flb::sum_columns(c->partials, nrows, 4, dev_sums + 4 * (size_t)t, c->stream);
+            }
+        } else {
+            se = c->ops->step(c->m, c->step, src, dst, c->drho, c->stream);
+        }
         if (tune) {
             c->m.zchunk = 0;
             FLB_CUDA(se);
@@ -563,6 +579,41 @@ int flb_step(flb_ctx* c, int nsteps)
             if (r2) return r2;
         }
     }
+    return FLB_OK;
+}
+
+int flb_step(flb_ctx* c, int nsteps)
+{
+    FLB_TRACE();
+    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(FLB_EINVAL, "nsteps must be >= 0");
+    DeviceGuard guard(c->device);
+    return step_impl(c, nsteps, nullptr);
+}
+
+int flb_step_sums(flb_ctx* c, int nsteps, double* sums)
+{
+    FLB_TRACE();
+    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(FLB_EINVAL, "nsteps must be >= 0");
+    if (nsteps > 0 && !sums) return fail(FLB_EINVAL, "sums is NULL");
+    if (nsteps == 0) return FLB_OK;
+    DeviceGuard guard(c->device);
+    int rc = ensure_partials(c);
+    if (rc) return rc;
+    if ((size_t)nsteps > c->ss_cap) {
+        if (c->ss_dev) cudaFree(c->ss_dev);
+        c->ss_dev = nullptr;
+        c->ss_cap = 0;
+        if ((rc = alloc((void**)&c->ss_dev, 4 * (size_t)nsteps * sizeof(double)))) return rc;
+        c->ss_cap = (size_t)nsteps;
+    }
+    if ((rc = step_impl(c, nsteps, c->ss_dev))) return rc;
+    FLB_CUDA(cudaMemcpyAsync(sums, c->ss_dev, 4 * (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+    FLB_CUDA(cudaStreamSynchronize(c->stream));
+    const double m0 = c->m.rho0 * (double)c->m.V;
+    for (int t = 0; t < nsteps; ++t) sums[4 * t] += m0;
     return FLB_OK;
 }
 

@@ -79,6 +79,11 @@ struct PrecOps {
     // pre-collision populations f_i at n sites (device list), out[i*n + k]
     cudaError_t (*get_sites)(const HostModel&, const void* src, const long long* sites, int n, double* out,
                              cudaStream_t);
+    // the step, also writing *nrows rows of 4 partial sums (mass deviation,
+    // momentum) of the state it steps from; cudaErrorNotSupported (nothing
+    // launched) where the step kernel does not provide them
+    cudaError_t (*step_rows)(const HostModel&, uint64_t step, const void* src, void* dst, const void* drho,
+                             double* rows, int* nrows, cudaStream_t);
 };
 
 const PrecOps& ops_fp64();

@@ -647,11 +647,16 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 // xb - 2.  Excess free energy only (pgrad = 0): the total-free-energy force
 // runs through k_step_march.
 // ---------------------------------------------------------------------------
-template <class S, int TXT, int TY, int MINB, int GX>
+// SUMS: the block also adds up the mass deviation and the momentum of the
+// state it steps from -- the density of each collided site from the density
+// ring, sum_i c_i g_i from its pulled populations -- and writes them as one
+// row of 4 doubles (rows[block * 4 + 0..3]; FP32 within a warp, FP64 above).
+template <class S, int TXT, int TY, int MINB, int GX, bool SUMS = false>
 __global__ void __launch_bounds__(TXT* TY, MINB)
-    k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<S> P)
+    k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<S> P, double* __restrict__ rows)
 {
     using A = Packed<S>;
+    F2 sum_r(0.f), sum_jx(0.f), sum_jy(0.f), sum_jz(0.f);
     using L = D3Q19;
     constexpr bool QUAD = GX == 4;
     constexpr int NT = TXT * TY;
@@ -827,6 +832,18 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                 else
                     g[i] = F2(A::plain1(p + x + 1), A::plain1(p + x2));
             }
+            if constexpr (SUMS) {
+                sum_r += mk2(*reinterpret_cast<const float2*>(srho[ra] + cr));
+#pragma unroll
+                for (int i = 1; i < L::Q; ++i) {
+                    if (Vel<L>::cx(i) > 0) sum_jx += g[i];
+                    if (Vel<L>::cx(i) < 0) sum_jx = sum_jx - g[i];
+                    if (Vel<L>::cy(i) > 0) sum_jy += g[i];
+                    if (Vel<L>::cy(i) < 0) sum_jy = sum_jy - g[i];
+                    if (Vel<L>::cz(i) > 0) sum_jz += g[i];
+                    if (Vel<L>::cz(i) < 0) sum_jz = sum_jz - g[i];
+                }
+            }
             const int s = x + X * y + XY * z;
             L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
 #pragma unroll
@@ -835,6 +852,22 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
         ra = ra1;
         mb = mb1;
         zc = zc == Z - 1 ? 0 : zc + 1;
+    }
+    if constexpr (SUMS) {
+        __shared__ double red[NT / 32][4];
+        float v[4] = {sum_r.v.x + sum_r.v.y, sum_jx.v.x + sum_jx.v.y, sum_jy.v.x + sum_jy.v.y,
+                      sum_jz.v.x + sum_jz.v.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        if ((tid & 31) == 0)
+            for (int k = 0; k < 4; ++k) red[tid >> 5][k] = (double)v[k];
+        __syncthreads();
+        if (tid < 4) {
+            double acc = 0.0;
+            for (int w = 0; w < NT / 32; ++w) acc += red[w][tid];
+            rows[4 * (blockIdx.x + (long)gridDim.x * (blockIdx.y + (long)gridDim.y * blockIdx.z)) + tid] = acc;
+        }
     }
 }
 

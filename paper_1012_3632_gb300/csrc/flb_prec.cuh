@@ -484,9 +484,20 @@ struct Prec {
             a, make_planes<S>(src, dst, L::Q, m.V), (const R*)drho);
         return cudaGetLastError();
     }
+    // The step; with rows (non-NULL) also the mass deviation and momentum of
+    // the state it steps from, as *nrows rows of 4 partial sums, where the
+    // step kernel provides them (cudaErrorNotSupported elsewhere, before any
+    // launch).
     static cudaError_t step(const HostModel& m, uint64_t t, const void* src, void* dst, const void* drho,
                             cudaStream_t st)
     {
+        return step_rows(m, t, src, dst, drho, nullptr, nullptr, st);
+    }
+    static cudaError_t step_rows(const HostModel& m, uint64_t t, const void* src, void* dst, const void* drho,
+                                 double* rows, int* nrows, cudaStream_t st)
+    {
+        if (rows && !(kPackedStorage && m.Q == 19 && m.nonideal && m.X % 2 == 0 && FLB_PACKED && !m.total))
+            return cudaErrorNotSupported;
         if (m.Q == 9 && m.nonideal && m.model == 1) {
             const StepArgs<R> a = make_args<D2Q9, R>(m, t);
             const dim3 b(32, 8, 1);
@@ -505,12 +516,19 @@ struct Prec {
                         const dim3 g((m.X + 2 * TXT - 1) / (2 * TXT), (m.Y + TY - 1) / TY,
                                      (m.Z + a.nzc - 1) / a.nzc);
                         // density gather by quads of sites when rows hold whole quads
-                        if (m.X % 4 == 0)
-                            k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 4>
-                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
-                        else
-                            k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 2>
-                                <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
+                        const Planes<S> pl = make_planes<S>(src, dst, 19, m.V);
+                        if (rows) *nrows = (int)(g.x * g.y * g.z);
+                        if (m.X % 4 == 0) {
+                            if (rows)
+                                k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 4, true><<<g, b, 0, st>>>(a, pl, rows);
+                            else
+                                k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 4><<<g, b, 0, st>>>(a, pl, nullptr);
+                        } else {
+                            if (rows)
+                                k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 2, true><<<g, b, 0, st>>>(a, pl, rows);
+                            else
+                                k_step_march2<S, TXT, TY, FLB_MARCH2_MINB, 2><<<g, b, 0, st>>>(a, pl, nullptr);
+                        }
                         return cudaGetLastError();
                     }
                 }
@@ -708,7 +726,7 @@ struct Prec {
     {
         static const PrecOps o = {(int)sizeof(S), (int)sizeof(R), density, step, init, get_pop, set_pop, moments,
                                   mu_force, mode_partials, cons_partials, mode_field, rows, needs_density,
-                                  pull_state, push_state, get_sites};
+                                  pull_state, push_state, get_sites, step_rows};
         return o;
     }
 };

@@ -29,7 +29,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 EXPORTS = [
     "flb_default_options", "flb_create", "flb_init", "flb_step", "flb_moments", "flb_structure_factor",
     "flb_snapshot_count", "flb_reset_accumulators", "flb_conservation", "flb_get_populations",
-    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_z_chunk", "flb_adjoint_segment", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
+    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_z_chunk", "flb_adjoint_segment", "flb_step_sums", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
     "flb_get_info", "flb_kernel_timing", "flb_kernel_times", "flb_save", "flb_load", "flb_error_string",
     "flb_last_error", "flb_destroy", "flb_structure_factor_noalloc",
     "flb_batch_create", "flb_batch_init", "flb_batch_step", "flb_batch_autotune", "flb_batch_mode_variance",
@@ -114,6 +114,7 @@ def lib():
         "flb_check_guards": (ctypes.c_int, [vp]),
         "flb_z_chunk": (ctypes.c_int, [vp, ip, ip]),
         "flb_adjoint_segment": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_int, vp, vp, vp]),
+        "flb_step_sums": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "flb_get_step": (ctypes.c_int, [vp, P(ctypes.c_uint64)]),
         "flb_set_step": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "flb_set_stream": (ctypes.c_int, [vp, vp]),
@@ -240,6 +241,12 @@ class Context:
 
     def step(self, n: int = 1):
         _check(lib().flb_step(self._h, int(n)))
+
+    def step_sums(self, nsteps: int = 1, out: np.ndarray | None = None) -> np.ndarray:
+        """nsteps steps; (nsteps, 4) mass and momentum of the state each step starts from."""
+        sums = out if out is not None else np.empty((nsteps, 4))
+        _check(lib().flb_step_sums(self._h, int(nsteps), _dptr(sums)))
+        return sums
 
     def get_populations(self) -> np.ndarray:
         f = np.empty((self.Q, self.V))

@@ -448,3 +448,35 @@ def test_z_chunk_changes_no_result(prec):
     assert np.abs(out[0] - want).max() <= TOL[prec]
     with pytest.raises(FLBError):
         Context(19, dims, precision=prec, free_energy=FE, z_chunk=-1, **kw)
+
+
+@pytest.mark.parametrize("Q,dims,prec,fe", [
+    (19, (24, 20, 70), "fp32", FE),   # step kernel's own sums, quad gather
+    (19, (18, 12, 9), "bf16", FE),    # pair gather, BF16 storage
+    (19, (16, 12, 10), "fp32", None),  # ideal step: reduction before each step
+    (19, (9, 8, 7), "fp64", FE),
+    (9, (20, 14, 1), "fp32", FE),
+])
+def test_step_sums_equal_conservation_before_each_step(Q, dims, prec, fe):
+    """flb_step_sums reports, for every step, the mass and momentum of the state
+    the step starts from (flb_conservation of that state), and steps exactly
+    as flb_step does."""
+    n = 6
+    rho = inputs.uniform_density(dims, seed=7)
+    kw = dict(kT=1e-5, omega_shear=1.1, seed=8, precision=prec)
+    V = int(np.prod(dims))
+    with Context(Q, dims, free_energy=fe, **kw) as a:
+        a.init(rho=rho)
+        want = []
+        for _ in range(n):
+            want.append(a.conservation())
+            a.step(1)
+        fa = a.get_populations()
+    with Context(Q, dims, free_energy=fe, **kw) as b:
+        b.init(rho=rho)
+        got = b.step_sums(n)
+        fb = b.get_populations()
+    assert np.array_equal(fa, fb)
+    want = np.array(want)
+    assert np.abs(got[:, 0] - want[:, 0]).max() <= 1e-12 * V + 1e-5
+    assert np.abs(got[:, 1:] - want[:, 1:]).max() <= 1e-5
