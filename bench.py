@@ -349,9 +349,10 @@ def adjoint_vs_plain(dims=(64, 64, 64), nsteps=200, every=20, precision="fp32"):
         g0 = torch.empty((19, V), dtype=dt, device="cuda")
         c.get_state_device(g0.data_ptr())
     cfg = dict(dims=dims, kT=1e-6, seed=5, precision=precision, nsteps=nsteps, every=every, nonideal=True, rho_c=1.0)
-    # warm-up of the loss (cuFFT loads and plans on its first use) and of the path
+    # warm-up of the loss (cuFFT loads and plans on its first use) and of the
+    # path, long enough for the step's column-length tuning
     density_spectrum_loss(g0, dims).item()
-    warm = dict(cfg, nsteps=2, every=1)
+    warm = dict(cfg, nsteps=40, every=20)
     th0 = torch.tensor([1.0, 1.0, 1.0, 0.02, -0.01, 0.1], dtype=torch.float64, requires_grad=True)
     density_spectrum_loss(run(g0.clone().requires_grad_(True), th0, warm), dims).backward()
     theta = torch.tensor([1.0, 1.0, 1.0, 0.02, -0.01, 0.1], dtype=torch.float64, requires_grad=True)

@@ -23,6 +23,11 @@ from .flb import D3Q19, Context
 
 THETA = ("omega_shear", "omega_bulk", "omega_ghost", "kappa", "A", "B")
 
+# planes per block of the z-marching step, tuned by the first forward pass on a
+# lattice shape and reused by later contexts of the same shape (the length
+# changes no result)
+_ZCHUNK: dict = {}
+
 
 def _context(dims, theta, cfg):
     th = [float(v) for v in theta.detach().cpu().tolist()]
@@ -32,7 +37,8 @@ def _context(dims, theta, cfg):
     return Context(D3Q19, dims, th[0], th[1], th[2], kT=cfg["kT"], free_energy=fe, seed=cfg["seed"],
                    precision=cfg["precision"], rho0=cfg.get("rho0", 1.0), replica=cfg.get("replica", 0),
                    noise_rho_local=cfg.get("noise_rho_local", True),
-                   stream=torch.cuda.current_stream().cuda_stream)
+                   stream=torch.cuda.current_stream().cuda_stream,
+                   z_chunk=_ZCHUNK.get((tuple(dims), cfg["precision"]), 0))
 
 
 class FLBRun(torch.autograd.Function):
@@ -55,6 +61,9 @@ class FLBRun(torch.autograd.Function):
                 ckpts.append(c)
         gN = torch.empty_like(g0)
         ctx.get_state_device(gN.data_ptr())
+        planes, tuning = ctx.z_chunk()
+        if not tuning:
+            _ZCHUNK[(dims, cfg["precision"])] = planes
         fctx.flb = ctx
         fctx.ckpts = ckpts
         fctx.nsteps, fctx.every = nsteps, every

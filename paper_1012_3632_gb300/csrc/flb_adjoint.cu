@@ -312,18 +312,24 @@ __global__ void k_add_rb(R* __restrict__ lam, const R* __restrict__ rb, long V)
     }
 }
 
-__global__ void k_add_grads(const double* __restrict__ colsum, double* __restrict__ grad, int nonideal)
+// Column c of the per-block rows summed (in the order of k_sum_columns) and
+// added to its parameter: columns (bulk, shear, ghost, kappa, A, B) go to
+// grad (omega_shear, omega_bulk, omega_ghost, kappa, A, B).  One block per
+// column; the free-energy columns only for the non-ideal fluid.
+__global__ void k_add_grads(const double* __restrict__ rows, int nrows, double* __restrict__ grad, int nonideal)
 {
-    if (threadIdx.x == 0) {
-        grad[0] += colsum[1];  // omega_shear
-        grad[1] += colsum[0];  // omega_bulk
-        grad[2] += colsum[2];  // omega_ghost
-        if (nonideal) {
-            grad[3] += colsum[3];  // kappa
-            grad[4] += colsum[4];  // A
-            grad[5] += colsum[5];  // B
-        }
+    __shared__ double sh[256];
+    const int c = blockIdx.x;
+    if (c >= 3 && !nonideal) return;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) acc += rows[(long)r * 6 + c];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
     }
+    if (threadIdx.x == 0) grad[c == 0 ? 1 : c == 1 ? 0 : c] += sh[0];
 }
 
 template <class R>
@@ -397,8 +403,7 @@ cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, 
         k_adj_rho<R><<<g, b, 0, st>>>(a, drho, mubar, rb1, lam, rb_out, rows);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = sum_columns(rows, nrows, 6, colsum, st)) != cudaSuccess) return e;
-    k_add_grads<<<1, 32, 0, st>>>(colsum, grad, m.nonideal);
+    k_add_grads<<<6, 256, 0, st>>>(rows, nrows, grad, m.nonideal);
     return cudaGetLastError();
 }
 
