@@ -362,7 +362,7 @@ AdjArgs<R> make_adj(const HostModel& m, const Coll<R>& c)
 
 template <class R>
 cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, const R* gn, const R* lam_next,
-                           const R* rb_next, R* lam, R* rb_out, R* work, double* rows, double* colsum, double* grad,
+                           const R* rb_next, R* lam, R* rb_out, R* work, double* rows, double* grad,
                            cudaStream_t st)
 {
     const long V = m.V;
@@ -410,15 +410,15 @@ cudaError_t adjoint_step_t(const HostModel& m, const Coll<R>& c, uint64_t step, 
 }  // namespace
 
 cudaError_t adjoint_step(const HostModel& m, int prec, uint64_t step, const void* gn, const void* lam_next,
-                         const void* rb_next, void* lam, void* rb_out, void* work, double* rows, double* colsum,
-                         double* grad, cudaStream_t st)
+                         const void* rb_next, void* lam, void* rb_out, void* work, double* rows, double* grad,
+                         cudaStream_t st)
 {
     if (prec == FLB_FP64)
         return adjoint_step_t<double>(m, coll_fp64(m, step), step, (const double*)gn, (const double*)lam_next,
                                       (const double*)rb_next, (double*)lam, (double*)rb_out, (double*)work, rows,
-                                      colsum, grad, st);
+                                      grad, st);
     return adjoint_step_t<float>(m, coll_fp32(m, step), step, (const float*)gn, (const float*)lam_next,
-                                 (const float*)rb_next, (float*)lam, (float*)rb_out, (float*)work, rows, colsum, grad,
+                                 (const float*)rb_next, (float*)lam, (float*)rb_out, (float*)work, rows, grad,
                                  st);
 }
 

@@ -119,7 +119,6 @@ struct flb_ctx {
     // adjoint scratch
     void* adj_work = nullptr;
     double* adj_rows = nullptr;
-    double* adj_col = nullptr;
     void* adj_lam2 = nullptr;  // flb_adjoint_segment: second adjoint state (ping-pong)
     void* adj_rb = nullptr;    // flb_adjoint_segment: deferred density parts (2 fields)
     double* ss_dev = nullptr;  // flb_step_sums: 4 sums per step (device)
@@ -177,7 +176,7 @@ int alloc_guarded(flb_ctx* c, void** p, size_t bytes, const char* name)
 void free_all(flb_ctx* c)
 {
     void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
-                    c->adj_work, c->adj_rows, c->adj_col, c->adj_lam2, c->adj_rb, c->ss_dev, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
+                    c->adj_work, c->adj_rows, c->adj_lam2, c->adj_rb, c->ss_dev, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
                     c->hs_tmp, c->sw_chol, c->sw_work, c->sw_xi};
     for (void* p : ptrs) {
         bool guarded = false;
@@ -936,11 +935,10 @@ int flb_adjoint_step(flb_ctx* c, const void* g_n, uint64_t step, const void* lam
     DeviceGuard guard(c->device);
     int rc;
     if ((rc = alloc(&c->adj_work, 10 * c->field_bytes())) ||
-        (rc = alloc((void**)&c->adj_rows, (size_t)flb::adjoint_rows(c->m) * 6 * sizeof(double))) ||
-        (rc = alloc((void**)&c->adj_col, 8 * sizeof(double))))
+        (rc = alloc((void**)&c->adj_rows, (size_t)flb::adjoint_rows(c->m) * 6 * sizeof(double))))
         return rc;
     FLB_CUDA(flb::adjoint_step(c->m, c->prec, step, g_n, lam_next, nullptr, lam, nullptr, c->adj_work, c->adj_rows,
-                               c->adj_col, grad, c->stream));
+                               grad, c->stream));
     return FLB_OK;
 }
 
@@ -956,7 +954,7 @@ int flb_adjoint_segment(flb_ctx* c, const void* g_start, uint64_t step0, int n, 
     int rc;
     if ((rc = alloc(&c->adj_work, 10 * c->field_bytes())) ||
         (rc = alloc((void**)&c->adj_rows, (size_t)flb::adjoint_rows(c->m) * 6 * sizeof(double))) ||
-        (rc = alloc((void**)&c->adj_col, 8 * sizeof(double))) || (rc = alloc(&c->adj_lam2, c->pop_bytes())) ||
+        (rc = alloc(&c->adj_lam2, c->pop_bytes())) ||
         (rc = alloc(&c->adj_rb, 2 * c->field_bytes())))
         return rc;
     const size_t pb = c->pop_bytes();
@@ -983,7 +981,7 @@ int flb_adjoint_segment(flb_ctx* c, const void* g_start, uint64_t step0, int n, 
     for (int k = n - 1; k >= 0; --k) {
         void* rb_out = defer ? rb + (size_t)(k & 1) * fb : nullptr;
         FLB_CUDA(flb::adjoint_step(c->m, c->prec, step0 + (uint64_t)k, S + (size_t)k * pb, nxt, rb_in, cur, rb_out,
-                                   c->adj_work, c->adj_rows, c->adj_col, grad, c->stream));
+                                   c->adj_work, c->adj_rows, grad, c->stream));
         rb_in = rb_out;
         std::swap(nxt, cur);
     }

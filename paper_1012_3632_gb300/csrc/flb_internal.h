@@ -130,15 +130,15 @@ cudaError_t height_power(const double* h, int X, double2* work, double2* scratch
 
 // Adjoint of one D3Q19 step (flb_adjoint.cu): gn, lam_next, lam are [19][V]
 // pre-collision deviations / adjoints in the storage type (FP64 or FP32);
-// work holds 10 V compute-type scalars, rows adjoint_rows(m) * 6 doubles,
-// colsum 6 doubles; grad (6 doubles) is incremented.  Within a segment the
+// work holds 10 V compute-type scalars, rows adjoint_rows(m) * 6 doubles;
+// grad (6 doubles, device) is incremented.  Within a segment the
 // density part of the adjoint (one scalar per site, added to every
 // population) may be passed on instead of added: rb_out (V scalars or NULL)
 // receives it and the next step takes it as rb_next (NULL: lam_next is
 // complete); adjoint_add_rb adds the last one.
 cudaError_t adjoint_step(const HostModel& m, int prec, uint64_t step, const void* gn, const void* lam_next,
-                         const void* rb_next, void* lam, void* rb_out, void* work, double* rows, double* colsum,
-                         double* grad, cudaStream_t st);
+                         const void* rb_next, void* lam, void* rb_out, void* work, double* rows, double* grad,
+                         cudaStream_t st);
 cudaError_t adjoint_add_rb(const HostModel& m, int prec, void* lam, const void* rb, cudaStream_t st);
 int adjoint_rows(const HostModel& m);
 
