@@ -216,8 +216,10 @@ __device__ __forceinline__ void fill_twiddles(double2* tw, int L, double2* scrat
     __syncthreads();
 }
 
+constexpr int kFftThreads = 256, kFftLoads = 4096 / kFftThreads;
+
 template <class T>
-__global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const LineGeom g, int B)
+__global__ void __launch_bounds__(kFftThreads) k_fft_lines(T* __restrict__ data, const FftPlan plan, const LineGeom g, int B)
 {
     using E = decltype(T::x);
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -235,17 +237,30 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
     // power-of-two lines (and line counts): shifts and masks for the indices
     const bool p2 = (L & (L - 1)) == 0, nl2 = (nl & (nl - 1)) == 0;
     const int lgL = __ffs(L) - 1, lgnl = __ffs(nl) - 1;
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        int l, j;
-        if (g.es == 1) {
-            l = p2 ? e >> lgL : e / L;
-            j = p2 ? e & (L - 1) : e % L;
-        } else {
-            l = nl2 ? e & (nl - 1) : e % nl;
-            j = nl2 ? e >> lgnl : e / nl;
+    // all of a thread's loads first (a block holds at most 4096 elements, so at
+    // most kFftLoads per thread at 256 threads), then the shared-memory stores:
+    // the loads are in flight together instead of one after another
+    T vin[kFftLoads];
+    int sidx[kFftLoads];
+#pragma unroll
+    for (int q = 0; q < kFftLoads; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < tot) {
+            int l, j;
+            if (g.es == 1) {
+                l = p2 ? e >> lgL : e / L;
+                j = p2 ? e & (L - 1) : e % L;
+            } else {
+                l = nl2 ? e & (nl - 1) : e % nl;
+                j = nl2 ? e >> lgnl : e / nl;
+            }
+            sidx[q] = p2 ? pad16(l * L + j) : l * L + j;
+            vin[q] = data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es];
         }
-        b0[p2 ? pad16(l * L + j) : l * L + j] = data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es];
     }
+#pragma unroll
+    for (int q = 0; q < kFftLoads; ++q)
+        if (threadIdx.x + q * blockDim.x < tot) b0[sidx[q]] = vin[q];
     __syncthreads();
     int Ns = 1;
     T* cur = b0;
@@ -287,16 +302,20 @@ __global__ void k_fft_lines(T* __restrict__ data, const FftPlan plan, const Line
         cur = nxt;
         nxt = tmp;
     }
-    for (int e = threadIdx.x; e < tot; e += blockDim.x) {
-        int l, j;
-        if (g.es == 1) {
-            l = p2 ? e >> lgL : e / L;
-            j = p2 ? e & (L - 1) : e % L;
-        } else {
-            l = nl2 ? e & (nl - 1) : e % nl;
-            j = nl2 ? e >> lgnl : e / nl;
+#pragma unroll
+    for (int q = 0; q < kFftLoads; ++q) {
+        const int e = threadIdx.x + q * blockDim.x;
+        if (e < tot) {
+            int l, j;
+            if (g.es == 1) {
+                l = p2 ? e >> lgL : e / L;
+                j = p2 ? e & (L - 1) : e % L;
+            } else {
+                l = nl2 ? e & (nl - 1) : e % nl;
+                j = nl2 ? e >> lgnl : e / nl;
+            }
+            data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es] = cur[p2 ? pad16(l * L + j) : l * L + j];
         }
-        data[(long)(i0 + l) * g.s_in + o1 + (long)j * g.es] = cur[p2 ? pad16(l * L + j) : l * L + j];
     }
 }
 
@@ -367,7 +386,7 @@ static cudaError_t fft_axis(T* data, T* scratch, int L, long es, long s_in, int 
         cudaError_t e = fft_smem_optin<T>();
         if (e != cudaSuccess) return e;
         const dim3 grid((n_in + B - 1) / B, n_out);
-        k_fft_lines<T><<<grid, 256, smem, s>>>(data, plan, g, B);
+        k_fft_lines<T><<<grid, kFftThreads, smem, s>>>(data, plan, g, B);
         return cudaGetLastError();
     }
     k_dft_lines_naive<T><<<1024, 256, 0, s>>>(data, scratch, g, n_out);
