@@ -80,3 +80,26 @@ def test_graft_entry_build_compiles_everything():
     g.build()
     assert os.path.exists(os.path.join(ROOT, "paper_1012_3632_gb300", "libflb.so"))
     assert os.path.exists(os.path.join(ROOT, "oracle", "liborc.so"))
+
+
+def test_null_context_rejected(flb):
+    """Every entry point that takes a context refuses NULL with FLB_EINVAL
+    before touching the device."""
+    L = flb.lib()
+    d = (ctypes.c_double * 64)()
+    ll = (ctypes.c_longlong * 2)(0, 1)
+    i1, i2 = ctypes.c_int(), ctypes.c_int()
+    calls = [
+        lambda: L.flb_step(None, 1),
+        lambda: L.flb_step_sums(None, 1, d),
+        lambda: L.flb_conservation(None, d),
+        lambda: L.flb_get_populations(None, d),
+        lambda: L.flb_get_sites(None, ll, 2, d),
+        lambda: L.flb_check_guards(None),
+        lambda: L.flb_z_chunk(None, ctypes.byref(i1), ctypes.byref(i2)),
+        lambda: L.flb_adjoint_step(None, None, 0, None, None, None),
+        lambda: L.flb_adjoint_segment(None, None, 0, 1, None, None, None),
+        lambda: L.flb_structure_factor(None, d, 0, 0),
+    ]
+    for k, call in enumerate(calls):
+        assert call() == flb.FLB_EINVAL, k
