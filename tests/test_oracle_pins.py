@@ -17,6 +17,8 @@ import pytest
 
 from oracle import theory
 
+from hydro_theory import fit_sound_wave, sound_wave_rates
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 GOLD = os.path.join(HERE, "golden")
 CS2 = 1.0 / 3.0
@@ -74,16 +76,17 @@ print(json.dumps([x & 0xFFFFFFFF for x in out.tolist()]))
 
 def test_philox_matches_library(orc):
     """Philox4x32-10 of the oracle equals the Philox of Triton's CPU interpreter
-    (a library routine; key = (seed lo, seed hi), 10 rounds)."""
-    pytest.importorskip("triton")
+    (a library routine; key = (seed lo, seed hi), 10 rounds).  This is the pin
+    of the oracle's noise generator, so a missing Triton or a failing
+    interpreter run fails the test instead of skipping it."""
+    import triton  # noqa: F401  (ImportError fails the test: the generator must not run unpinned)
     rng = np.random.default_rng(7)
     ctrs = [[0, 0, 0, 0], [1, 2, 3, 4], [0xFFFFFFFF] * 4]
     ctrs += [list(map(int, rng.integers(0, 2**32, 4, dtype=np.uint64))) for _ in range(13)]
     seed = 0x1234567890ABCDEF
     r = subprocess.run([sys.executable, "-c", _TRITON_SCRIPT, json.dumps({"ctr": ctrs, "seed": seed})],
                        capture_output=True, text=True, timeout=600)
-    if r.returncode != 0:
-        pytest.skip("Triton interpreter unavailable: " + r.stderr[-300:])
+    assert r.returncode == 0, "Triton interpreter run failed: " + r.stderr[-600:]
     lib = json.loads(r.stdout.strip().splitlines()[-1])
     key = [seed & 0xFFFFFFFF, seed >> 32]
     mine = []
@@ -427,6 +430,39 @@ def test_shear_wave_decay(orc, Q):
     k = 2 * np.pi / Lz
     expect = theory.shear_viscosity(om) * k * k
     assert abs(rate / expect - 1) < 5e-3
+
+
+@pytest.mark.parametrize("Q", [9, 19])
+def test_sound_wave_attenuation(orc, Q):
+    """A density wave delta rho = 1e-4 cos(k x), k = 2 pi / 128, at kT = 0 with
+    three distinct rates (shear 1.3, bulk 0.8, ghost 1.7) propagates at cs and
+    decays at the rate that the App. B viscosities with the Sec. V map give
+    (closed form above), within 0.5 %.  This pins which mode carries omega_bulk:
+    the bulk rate on a ghost mode, or the ghost rate on the c^2 mode, changes
+    Gamma by a factor 2.4-3 at these rates."""
+    Lx, om = 128, dict(omega_shear=1.3, omega_bulk=0.8, omega_ghost=1.7)
+    p = orc.Params(Q=Q, dims=(Lx, 1, 1), **om)
+    L = orc.lattice(Q)
+    k = 2 * np.pi / Lx
+    x = np.arange(Lx)
+    f = orc.init(p, rho=1.0 + 1e-4 * np.cos(k * x))
+    e = np.exp(-1j * k * x)
+    cx = L.c[:, 0].astype(float)
+    ts, rk, jk = [], [], []
+    f = orc.run(p, f, 0, 100)  # kinetic transients decay within a few steps
+    t = 100
+    while t <= 1500:
+        ts.append(t)
+        rk.append((f.sum(0) - 1.0) @ e)
+        jk.append((cx @ f) @ e)
+        f = orc.run(p, f, t, 10)
+        t += 10
+    gamma, omega = fit_sound_wave(np.array(ts), rk, jk)
+    gamma_th, omega_th = sound_wave_rates(L.D, k, om["omega_shear"], om["omega_bulk"])
+    assert abs(gamma / gamma_th - 1) < 5e-3, (gamma, gamma_th)
+    assert abs(omega / omega_th - 1) < 5e-3, (omega, omega_th)
+    swapped, _ = sound_wave_rates(L.D, k, om["omega_shear"], om["omega_ghost"])
+    assert abs(swapped / gamma_th - 1) > 0.5  # the pin can tell the two rates apart
 
 
 @pytest.mark.parametrize("Q", [9, 19])
