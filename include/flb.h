@@ -384,14 +384,17 @@ int flb_batch_synchronize(flb_batch* b);
 void flb_batch_destroy(flb_batch* b);
 
 /* Structure factor that allocates nothing.  For callers that cannot allocate
- * device memory while they run -- code captured into a CUDA graph, hosts whose
- * allocator forbids cudaMalloc after start-up, real-time loops with a fixed
- * memory budget -- this computes, from buffers the caller already owns, the
- * same S_a(k) as flb_structure_factor (accumulate = 0).  The paper has no
- * counterpart: it is an interface variant of flb_structure_factor.
- *   lattice  FLB_D2Q9 or FLB_D3Q19;  dims as in flb_create, with at most
- *            FLB_NOALLOC_MAX_SITES sites and every edge a product of 2, 3 and 5
- *            (up to 4096); anything else returns FLB_EINVAL before any GPU work
+ * device memory while they run -- hosts whose allocator forbids cudaMalloc
+ * after start-up (a serving process that sizes its device memory once),
+ * real-time loops with a fixed memory budget, code running where an
+ * allocation would synchronise the device -- this computes, from buffers the
+ * caller already owns, the same S_a(k) as flb_structure_factor
+ * (accumulate = 0).  The paper has no counterpart: it is an interface variant
+ * of flb_structure_factor.
+ *   lattice  FLB_D2Q9 or FLB_D3Q19;  dims as in flb_create, every edge a
+ *            product of 2, 3 and 5 (up to 4096) and at most
+ *            FLB_NOALLOC_MAX_SITES sites in all; anything else returns
+ *            FLB_EINVAL before any GPU work
  *   f        device pointer: pre-collision populations f^LB, Q*V doubles in the
  *            layout f[i*V + s] (what flb_get_populations returns), read only
  *   mode     0 = density, else the mode index of the basis above
@@ -400,12 +403,16 @@ void flb_batch_destroy(flb_batch* b);
  *            call returns after enqueueing, without synchronising
  * The FFT work array is a static device array of FLB_NOALLOC_MAX_SITES complex
  * doubles (16 MiB) that every GPU which loads the library holds until the
- * process exits.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current: make that first
- * call before any stream capture.  Every call uses the same array, so calls
- * that may overlap on the GPU (unordered streams) race and must be serialised
- * by the caller.  No cudaMalloc, cudaFree or allocating library routine is
- * called. */
+ * process exits.  The first call on a device sets that device up: with the
+ * device current it looks up the array's device address
+ * (cudaGetSymbolAddress), reads the SM count and raises the FFT kernel's
+ * shared-memory limit; make that first call before any stream capture.  The
+ * look-up is kept for the life of the process: after a cudaDeviceReset in the
+ * caller's process this entry point must not be called again.  Every call
+ * uses the same array, which keeps the last call's contents (each call
+ * overwrites all of the part it reads), so calls that may overlap on the GPU
+ * (unordered streams, several host threads) race and must be serialised by the
+ * caller.  No cudaMalloc, cudaFree or allocating library routine is called. */
 #define FLB_NOALLOC_MAX_SITES (1 << 20)
 int flb_structure_factor_noalloc(int lattice, const int dims[3], const double* f, int mode, double* S,
                                  void* stream);

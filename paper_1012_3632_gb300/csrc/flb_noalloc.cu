@@ -1,11 +1,12 @@
 // flb_noalloc.cu -- structure factor that allocates nothing.
 //
-// Some callers cannot allocate device memory while they run: code that is
-// captured into a CUDA graph, hosts whose allocator forbids cudaMalloc after
-// start-up, or real-time loops whose memory budget is fixed up front.  This
-// entry point gives them the structure factor of flb_structure_factor from
-// device buffers they already own; its FFT work array is a file-scope static
-// device array instead of memory obtained from cudaMalloc.
+// Some callers cannot allocate device memory while they run: hosts whose
+// allocator forbids cudaMalloc after start-up (a serving process that sizes
+// its device memory once), real-time loops whose memory budget is fixed up
+// front, or code running where an allocation would synchronise the device.
+// This entry point gives them the structure factor of flb_structure_factor
+// from device buffers they already own; its FFT work array is a file-scope
+// static device array instead of memory obtained from cudaMalloc.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -21,22 +22,33 @@ namespace {
 // that loads the library keeps it until the process exits.
 __device__ __align__(256) double2 g_sf_work[FLB_NOALLOC_MAX_SITES];
 
-// Device address of g_sf_work per device, looked up once with that device
-// current (in host code the symbol is a host-side stand-in, not an address).
+// Per device, looked up once with that device current: the device address of
+// g_sf_work (in host code the symbol is a host-side stand-in, not an address)
+// and the number of SMs, which sizes the grid.  The entries live until the
+// process exits; a cudaDeviceReset by the caller invalidates them.
 constexpr int kMaxDevices = 128;
-double2* g_work_addr[kMaxDevices] = {nullptr};
-std::mutex g_work_mutex;
+struct DeviceSlot {
+    double2* work;
+    int sms;
+};
+DeviceSlot g_slot[kMaxDevices] = {};
+std::mutex g_slot_mutex;
 
-cudaError_t work_address(int dev, double2** out)
+cudaError_t device_slot(int dev, DeviceSlot* out)
 {
-    std::lock_guard<std::mutex> lock(g_work_mutex);
-    if (!g_work_addr[dev]) {
+    std::lock_guard<std::mutex> lock(g_slot_mutex);
+    DeviceSlot& d = g_slot[dev];
+    if (!d.work) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_sf_work);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_sf_work);
         if (e != cudaSuccess) return e;
-        g_work_addr[dev] = static_cast<double2*>(p);
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        d.sms = sms > 0 ? sms : 1;
+        d.work = static_cast<double2*>(p);
     }
-    *out = g_work_addr[dev];
+    *out = d;
     return cudaSuccess;
 }
 
@@ -69,29 +81,31 @@ extern "C" int flb_structure_factor_noalloc(int lattice, const int dims[3], cons
     for (int d = 0; d < 3; ++d)
         if (dims[d] < 1) return flb::set_error(FLB_EINVAL, "every dimension must be >= 1");
     if (lattice == FLB_D2Q9 && dims[2] != 1) return flb::set_error(FLB_EINVAL, "D2Q9 needs dims[2] == 1");
+    // edges first: each is then at most 4096, so their product fits in a long
+    for (int d = 0; d < 3; ++d)
+        if (!flb::fft_length_in_place(dims[d]))
+            return flb::set_error(FLB_EINVAL, "edge length " + std::to_string(dims[d]) +
+                                                  " is not a product of 2, 3 and 5 (up to 4096)");
     const long V = (long)dims[0] * dims[1] * dims[2];
     if (V > FLB_NOALLOC_MAX_SITES)
         return flb::set_error(FLB_EINVAL, "lattice has " + std::to_string(V) + " sites; the allocation-free "
                                           "structure factor handles at most FLB_NOALLOC_MAX_SITES = " +
                                               std::to_string(FLB_NOALLOC_MAX_SITES));
-    for (int d = 0; d < 3; ++d)
-        if (!flb::fft_length_in_place(dims[d]))
-            return flb::set_error(FLB_EINVAL, "edge length " + std::to_string(dims[d]) +
-                                                  " is not a product of 2, 3 and 5 (up to 4096)");
     if (mode < 0 || mode >= lattice) return flb::set_error(FLB_EINVAL, "mode out of range");
 
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return flb::set_error(FLB_ECUDA, std::string("no usable current device: ") + cudaGetErrorString(e));
-    double2* work = nullptr;
-    e = work_address(dev, &work);
+    DeviceSlot slot;
+    e = device_slot(dev, &slot);
     if (e != cudaSuccess)
-        return flb::set_error(FLB_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return flb::set_error(FLB_ECUDA, std::string("device set-up of the work array: ") + cudaGetErrorString(e));
+    double2* work = slot.work;
 
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     long nb = (V + 255) / 256;
-    if (nb > 152 * 16) nb = 152 * 16;
+    if (nb > 16L * slot.sms) nb = 16L * slot.sms;
     if (lattice == FLB_D3Q19)
         k_mode_of_populations<flb::D3Q19><<<(unsigned)nb, 256, 0, st>>>(f, mode, work, V);
     else

@@ -22,7 +22,7 @@ OMG = [1.0, 1.3, 1.2, 0.7, 1.5]
 
 
 def test_batch_replicas_match_oracle_and_single_lattice():
-    steps = 30
+    steps = 100
     with Batch(DIMS, OMS, KTS, SEEDS, omega_bulk=OMB, omega_ghost=OMG) as b:
         b.init(thermal=True)
         b.step(steps)

@@ -1,5 +1,6 @@
 """flb_structure_factor_noalloc: the structure factor for callers that cannot
-allocate device memory (graph-captured code, fixed-budget allocators).
+allocate device memory while they run (allocators that forbid cudaMalloc after
+start-up, fixed-budget real-time loops).
 
 It reads populations from a device buffer the caller owns, writes S_a(k) into
 another caller-owned device buffer and uses a static device work array, so it
@@ -43,12 +44,31 @@ def test_noalloc_matches_structure_factor_on_two_calls(lattice, dims, modes):
             assert np.allclose(got, want, rtol=1e-10, atol=1e-18)
 
 
+@pytest.mark.parametrize("mode", [0, 18])
+def test_noalloc_at_the_maximum_size(mode):
+    """D3Q19 128x128x64 = FLB_NOALLOC_MAX_SITES sites, the one size that fills
+    the static work array: element by element equal to flb_structure_factor."""
+    torch = pytest.importorskip("torch")
+    dims = (128, 128, 64)
+    assert dims[0] * dims[1] * dims[2] == 1 << 20
+    with Context(19, dims, precision="fp64", kT=1e-4, omega_shear=1.2, omega_bulk=0.9, omega_ghost=1.4,
+                 seed=5) as ctx:
+        ctx.init(thermal=True)
+        ctx.step(2)
+        want = ctx.structure_factor(mode)
+        f = ctx.get_populations()
+    for _ in range(2):  # two calls in a row on the same state
+        got = _noalloc(torch, 19, dims, f, mode)
+        assert np.allclose(got, want, rtol=1e-10, atol=1e-18)
+
+
 def test_noalloc_rejects_unsupported_sizes():
     torch = pytest.importorskip("torch")
     L = flb.lib()
     f_dev = torch.zeros(19, dtype=torch.float64, device="cuda")
     S_dev = torch.zeros(1, dtype=torch.float64, device="cuda")
-    for dims in ((1024, 1024, 2), (7, 4, 4)):  # too many sites; edge with a prime factor 7
+    # too many sites; an edge with a prime factor 7; edges whose product overflows 32 bits
+    for dims in ((1024, 1024, 2), (7, 4, 4), (4096, 4096, 4096), (2 ** 30, 2 ** 30, 2 ** 30)):
         d = (ctypes.c_int * 3)(*dims)
         rc = L.flb_structure_factor_noalloc(19, d, ctypes.c_void_p(f_dev.data_ptr()), 0,
                                             ctypes.c_void_p(S_dev.data_ptr()), None)
