@@ -247,6 +247,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def host_description():
+    """Logical CPU count and CPU model of the host the oracle runs on."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "cpu_model": model or platform.processor() or platform.machine(),
+            "machine": platform.machine()}
+
+
 def cpu_baseline(wl, budget_s=12.0):
     """Time the FP64 oracle (single thread) on a periodic 64^3 (D3Q19) lattice with
     the workload's parameters; steps are added until about budget_s of CPU work."""
@@ -270,15 +287,18 @@ def cpu_baseline(wl, budget_s=12.0):
     dt = time.perf_counter() - t0
     V = int(np.prod(dims))
     return {"value": V * steps / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{dims[0]}x{dims[1]}x{dims[2]} periodic lattice, same parameters, {steps} steps, "
-                      f"FP64 C oracle, single thread"}
+            "sample": f"{dims[0]}x{dims[1]}x{dims[2]} periodic lattice, same parameters, {steps} steps "
+                      f"(about {budget_s:.0f} s of CPU work), FP64 C oracle, single thread",
+            "host": host_description()}
 
 
-def batched_vs_plain(n=64, steps=200, seed=4):
-    """Batched ensemble (64 D3Q19 ideal-gas replicas, cubic sizes drawn from
-    {32,48,64,96,128}, omega_shear ~ U(0.8,1.6), kT = 1e-5, FP32, one persistent
-    launch per step replayed from a CUDA graph) against the plain single-lattice
-    step on the same replicas.  Returns site updates per second of both."""
+def batched_vs_plain(n=64, steps=2000, every=20, seed=4):
+    """The batched ensemble workload: 64 D3Q19 ideal-gas replicas, cubic sizes
+    drawn from {32,48,64,96,128}, omega_shear ~ U(0.8,1.6), kT = 1e-5, FP32, one
+    persistent launch per step replayed from a CUDA graph, 2000 steps with the
+    ensemble observables accumulated in FP64 every 20 steps (every replica's
+    mode variances and its density S(k) on the device).  Times the whole run,
+    the steps alone, and the plain single-lattice step on the same replicas."""
     import numpy as np
     import torch
 
@@ -295,11 +315,27 @@ def batched_vs_plain(n=64, steps=200, seed=4):
         shapes = b.autotune()
         b.step(20)
         torch.cuda.synchronize()
+        # the steps alone (graph replays)
         ev0.record(stream)
-        b.step(steps)
+        b.step(200)
         ev1.record(stream)
         torch.cuda.synchronize()
-        t_batch = ev0.elapsed_time(ev1) / steps  # ms per ensemble step
+        t_batch = ev0.elapsed_time(ev1) / 200  # ms per ensemble step
+        # the whole ensemble run: steps plus FP64 snapshot accumulation
+        b.init(thermal=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps // every):
+            b.step(every)
+            var = b.mode_variance()
+            for r in range(n):
+                b.structure_factor(r, 0, accumulate=True, fetch=False)
+        torch.cuda.synchronize()
+        t_run = time.perf_counter() - t0
+    kT = 1e-5
+    N = np.array([1, 1 / 3, 1 / 3, 1 / 3, 2 / 3, 4 / 3, 4 / 9, 1 / 9, 1 / 9, 1 / 9, 2 / 27, 2 / 27, 2 / 27,
+                  2 / 9, 2 / 9, 2 / 9, 2 / 9, 1 / 3, 1 / 9])
+    T = (var / N / 3.0) / kT  # mode temperatures / kT, per replica
     # plain: one context per replica size, time per step times the count
     t_plain = 0.0
     for l in sorted(set(int(v) for v in L)):
@@ -317,8 +353,16 @@ def batched_vs_plain(n=64, steps=200, seed=4):
     return {"workload": f"{n} D3Q19 ideal-gas replicas, cubic sizes from {{32,48,64,96,128}} (seed {seed}), "
                         "omega_shear U(0.8,1.6), kT=1e-5, FP32, graph-replayed persistent launch",
             "sites": sites, "batched_mlups": sites / (t_batch * 1e-3) / 1e6,
+            "batched_gbs": 152 * sites / (t_batch * 1e-3) / 1e9,
             "plain_mlups": sites / (t_plain * 1e-3) / 1e6, "batched_over_plain": t_plain / t_batch,
-            "ms_per_ensemble_step": t_batch, "tile_shape_per_size": shape_of}
+            "ms_per_ensemble_step": t_batch, "tile_shape_per_size": shape_of,
+            "ensemble_run": {"steps": steps, "snapshot_every": every, "seconds": t_run,
+                             "mlups_with_snapshots": sites * steps / t_run / 1e6,
+                             "what": "steps from a thermal start, every 20 steps flb_batch_mode_variance "
+                                     "(all replicas, FP64) and flb_batch_structure_factor(mode 0, accumulate) "
+                                     "for each replica on the device",
+                             "mode_temperature_over_kT_ensemble_mean_range": [float(T[:, 4:].mean(0).min()),
+                                                                               float(T[:, 4:].mean(0).max())]}}
 
 
 def adjoint_vs_plain(dims=(64, 64, 64), nsteps=200, every=20, precision="fp32"):
@@ -416,7 +460,8 @@ def run_reference(args, wl, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(args, wl),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_description()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -509,6 +554,10 @@ def main():
         scratch = torch.empty(int(2 * L2_BYTES) // 4, dtype=torch.float32, device=f"cuda:{local}")
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
+    # the library brackets every step-kernel launch with CUDA events on its
+    # stream (flb_kernel_timing) inside the timed region, so the kernel's own
+    # time is part of, and never exceeds, the step time
+    ctx.kernel_timing(True)
     with ClockSampler(local) as clk:
         time.sleep(0.3)
         barrier()
@@ -526,15 +575,10 @@ def main():
         torch.cuda.synchronize()
         barrier()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in evs) if flush else ev0.elapsed_time(ev1)
-    z_planes, z_tuning = ctx.z_chunk()
-    # per-kernel launch times: CUDA events around every launch, on a separate
-    # pass so that they do not load the timed region
-    n_kt = min(args.steps, 200)
-    ctx.kernel_timing(True)
-    ctx.step(n_kt)
-    ctx.synchronize()
     kms, kn = ctx.kernel_times()
     ctx.kernel_timing(False)
+    n_kt = args.steps
+    z_planes, z_tuning = ctx.z_chunk()
     ms_max = max_over_ranks(ms, world)
     value = whole_job_mlups(world, V, args.steps, ms_max * 1e-3)
 
@@ -565,7 +609,8 @@ def main():
            "what": "flb_init from a pinned host density field; per step flb_step_sums (the step, and the FP64 mass "
                    "and momentum of the state it starts from read back to the host); flb_moments(RHO) to pinned "
                    "host at the end",
-           "mass_drift": float(abs(sums[-1, 0] - sums[0, 0]) / abs(sums[0, 0]))}
+           "mass_drift": float(abs(sums[-1, 0] - sums[0, 0]) / abs(sums[0, 0])),
+           "host_round_trip_ms_per_step": t_e2e * 1e3 / args.steps - ms / args.steps}
 
     ctx.close()
     if rank != 0:
@@ -597,7 +642,10 @@ def main():
                      "bytes_per_site": fused_b, "sites_per_launch": V,
                      "avg_launch_ms": t_fused * 1e3,
                      "dram_min_bytes_per_site": fused_min,
-                     "frac_of_dram_min": fused_min * V / t_fused / 1e9 / peak},
+                     "frac_of_dram_min": fused_min * V / t_fused / 1e9 / peak,
+                     "achieved_dram_gbs": traffic / t_fused / 1e9 if traffic else None,
+                     "frac_dram": traffic / t_fused / 1e9 / peak if traffic else None,
+                     "dram_bytes_per_site": traffic / V if traffic else None},
         "kernels": {"density_gather": {"launches": int(kn[0]), "avg_ms": kms[0] / max(kn[0], 1),
                                        "bytes_per_site": gather_b,
                                        "achieved_gbs": gather_b * V / (kms[0] / max(kn[0], 1) * 1e-3) / 1e9

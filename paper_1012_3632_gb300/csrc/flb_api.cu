@@ -573,7 +573,7 @@ static int step_impl(flb_ctx* c, int nsteps, double* dev_sums)
                 if (!std::isfinite(v))
                     return fail(FLB_EDIVERGED, "non-finite mass or momentum at step " + std::to_string(c->step));
         }
-        if (c->ev_used > 8192) {
+        if (c->ev_used > 65536) {
             int r2 = timer_flush(c);
             if (r2) return r2;
         }

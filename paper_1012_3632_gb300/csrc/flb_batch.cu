@@ -475,20 +475,24 @@ int flb_batch_mode_variance(flb_batch* b, double* out)
         int rows = 0;
         for (int r = 0; r < b->n; ++r) rows = std::max(rows, ops.partial_rows_max(b->m[r]));
         BCUDA(cudaMalloc(&b->partials, (size_t)rows * 38 * sizeof(double)));
-        BCUDA(cudaMalloc(&b->red, 64 * sizeof(double)));
+        BCUDA(cudaMalloc(&b->red, (size_t)b->n * 38 * sizeof(double)));
     }
     b->mv_count += 1;
+    // every replica's 38 column sums into its own row of red (the partial-sum
+    // rows are reused in stream order), then one copy and one wait
     for (int r = 0; r < b->n; ++r) {
         int nrows = 0;
         BCUDA(ops.mode_partials(b->m[r], rep_src(b, r), b->partials, &nrows, b->stream));
-        BCUDA(flb::sum_columns(b->partials, nrows, 38, b->red, b->stream));
-        double h[38];
-        BCUDA(cudaMemcpyAsync(h, b->red, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
-        BCUDA(cudaStreamSynchronize(b->stream));
+        BCUDA(flb::sum_columns(b->partials, nrows, 38, b->red + 38 * (size_t)r, b->stream));
+    }
+    std::vector<double> h((size_t)b->n * 38);
+    BCUDA(cudaMemcpyAsync(h.data(), b->red, h.size() * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    BCUDA(cudaStreamSynchronize(b->stream));
+    for (int r = 0; r < b->n; ++r) {
         const double V = (double)b->m[r].V;
         for (int a = 0; a < 19; ++a) {
-            const double mean = h[a] / V;
-            b->mv_sum[19 * r + a] += h[19 + a] / V - mean * mean;
+            const double mean = h[38 * r + a] / V;
+            b->mv_sum[19 * r + a] += h[38 * r + 19 + a] / V - mean * mean;
             out[19 * r + a] = b->mv_sum[19 * r + a] / b->mv_count;
         }
     }

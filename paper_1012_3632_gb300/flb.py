@@ -429,10 +429,13 @@ class Batch:
         _check(lib().flb_batch_mode_variance(self._h, _dptr(out)))
         return out
 
-    def structure_factor(self, replica, mode=0, accumulate=False):
+    def structure_factor(self, replica, mode=0, accumulate=False, fetch=True):
+        """S_a(k) of one replica; with fetch=False (and accumulate=True) the
+        snapshot only goes into the device accumulator and None is returned."""
         X, Y, Z = self.dims[replica]
-        S = np.empty(X * Y * Z)
-        _check(lib().flb_batch_structure_factor(self._h, replica, _dptr(S), mode, int(bool(accumulate))))
+        S = np.empty(X * Y * Z) if fetch else None
+        _check(lib().flb_batch_structure_factor(self._h, replica, None if S is None else _dptr(S), mode,
+                                                int(bool(accumulate))))
         return S
 
     def get_populations(self, replica):
