@@ -102,7 +102,7 @@ def step_bytes(wl):
     return 3 * Q * e + 2 * rb, 0, 2 * Q * e
 
 
-KERNEL_SOURCES = ("flb_device.cuh", "flb_kernels.cuh", "flb_nextrho.cuh", "flb_prec.cuh")
+KERNEL_SOURCES = ("flb_device.cuh", "flb_kernels.cuh", "flb_prec.cuh")
 
 
 def max_over_ranks(x: float, world: int, device="cuda") -> float:
@@ -165,8 +165,6 @@ def kernel_name(wl):
     if wl["fe"] and wl["fe"].get("model", 0) == 1:
         return "k_step_swift"
     if wl["fe"] and wl["lattice"] == 19:
-        if packed and not wl["fe"].get("total") and wl["dims"][0] % 32 == 0 and wl["dims"][1] % 8 == 0:
-            return "k_step_nextrho"
         return "k_step_march2" if packed else "k_step_march"
     return "k_step2" if packed else "k_step"
 
@@ -621,10 +619,6 @@ def main():
         return
 
     fused_b, gather_b, fused_min = step_bytes(wl)
-    # the step that leaves the next step's density as per-tile parts also
-    # writes and reads them once: 4 B of own-tile part per site and 84 ring
-    # parts per 32 x 8 tile
-    kernel_min = fused_min + (2 * (4 + 84 * 4 / 256) if kernel_name(wl) == "k_step_nextrho" else 0)
     peak, peak_kind = measured_peak()
     n_fused = int(kn[1])
     t_fused = kms[1] / max(n_fused, 1) * 1e-3
@@ -649,8 +643,6 @@ def main():
                      "avg_launch_ms": t_fused * 1e3,
                      "dram_min_bytes_per_site": fused_min,
                      "frac_of_dram_min": fused_min * V / t_fused / 1e9 / peak,
-                     "kernel_dram_min_bytes_per_site": kernel_min,
-                     "frac_of_kernel_dram_min": kernel_min * V / t_fused / 1e9 / peak,
                      "achieved_dram_gbs": traffic / t_fused / 1e9 if traffic else None,
                      "frac_dram": traffic / t_fused / 1e9 / peak if traffic else None,
                      "dram_bytes_per_site": traffic / V if traffic else None},

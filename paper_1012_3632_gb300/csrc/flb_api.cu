@@ -90,15 +90,6 @@ struct flb_ctx {
 
     void* buf[2] = {nullptr, nullptr};  // post-collision populations of the last step
     int cur = 0;
-    // force-model steps that leave the next step's density as per-tile parts
-    // (ops->nextrho): the parts of the current state and of the next one, the
-    // column-end pieces, and whether rho_part[rho_cur] belongs to buf[cur]
-    // (every call that writes the populations clears rho_valid; the next step
-    // then first computes the parts of the state it finds)
-    float* rho_part[2] = {nullptr, nullptr};
-    float* rho_ext = nullptr;
-    int rho_cur = 0;
-    bool rho_valid = false;
     void* drho = nullptr;               // density deviation field (compute type)
     void* mu = nullptr;                 // chemical potential (observables)
     void* F = nullptr;                  // force field, 3 components (observables)
@@ -184,8 +175,7 @@ int alloc_guarded(flb_ctx* c, void** p, size_t bytes, const char* name)
 
 void free_all(flb_ctx* c)
 {
-    void* ptrs[] = {c->buf[0], c->buf[1], c->rho_part[0], c->rho_part[1], c->rho_ext, c->drho, c->mu, c->F,
-                    c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
+    void* ptrs[] = {c->buf[0], c->buf[1], c->drho, c->mu, c->F, c->partials, c->red, c->fft, c->fft_scratch, c->sk_tmp,
                     c->adj_work, c->adj_rows, c->adj_lam2, c->adj_rb, c->ss_dev, c->h_dev, c->hs_work, c->hs_scratch, c->hs_acc,
                     c->hs_tmp, c->sw_chol, c->sw_work, c->sw_xi};
     for (void* p : ptrs) {
@@ -456,24 +446,6 @@ int flb_create(flb_ctx** out, int lattice, const int dims[3], double omega_shear
         delete c;
         return rc;
     }
-    if (c->ops->nextrho(m)) {
-        // density parts: V own-tile parts and Z ntiles 84 ring parts per state;
-        // column-end pieces for the most columns any column length in use can
-        // give (the tuned lengths give at most ceil(Z / 12) columns)
-        const size_t ntiles = (size_t)(m.X / 32) * (m.Y / 8);
-        const size_t part = (size_t)m.V + (size_t)m.Z * ntiles * 84;
-        size_t ncol = std::max<size_t>(1, (m.Z + 11) / 12);
-        ncol = std::max<size_t>(ncol, (m.Z + flb::kZChunkDefault - 1) / flb::kZChunkDefault);
-        if (m.zchunk > 0) ncol = std::max<size_t>(ncol, (m.Z + m.zchunk - 1) / m.zchunk);
-        const size_t ext = 3 * ncol * ((size_t)m.X * m.Y + ntiles * 84);
-        if ((rc = alloc_guarded(c, (void**)&c->rho_part[0], part * sizeof(float), "density parts 0")) ||
-            (rc = alloc_guarded(c, (void**)&c->rho_part[1], part * sizeof(float), "density parts 1")) ||
-            (rc = alloc_guarded(c, (void**)&c->rho_ext, ext * sizeof(float), "density column ends"))) {
-            free_all(c);
-            delete c;
-            return rc;
-        }
-    }
     if (m.nonideal && m.model == 1 && m.kT > 0.0) {
         std::vector<double> chol(3 * (size_t)m.V);
         std::string err;
@@ -533,7 +505,6 @@ int flb_init(flb_ctx* c, const double* rho, const double* u, int thermal_init)
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (d_rho) cudaFree(d_rho);
     if (d_u) cudaFree(d_u);
-    c->rho_valid = false;
     if (e != cudaSuccess) return fail(FLB_ECUDA, std::string("flb_init: ") + cudaGetErrorString(e));
     c->cur = 0;
     c->step = 0;
@@ -546,19 +517,11 @@ int flb_init(flb_ctx* c, const double* rho, const double* u, int thermal_init)
 // dev_sums[0] holds the mass deviation (the caller adds rho0 V).
 static int step_impl(flb_ctx* c, int nsteps, double* dev_sums)
 {
-    const bool nextrho = c->ops->nextrho(c->m) != 0;
     for (int t = 0; t < nsteps; ++t) {
         const void* src = c->buf[c->cur];
         void* dst = c->buf[c->cur ^ 1];
         size_t slot = 0;
         int rc;
-        if (nextrho && !c->rho_valid) {
-            // the state came from outside the step: its density parts first
-            if ((rc = timer_begin(c, 0, &slot))) return rc;
-            FLB_CUDA(c->ops->rho_parts(c->m, src, c->rho_part[c->rho_cur], c->stream));
-            if ((rc = timer_end(c, slot))) return rc;
-            c->rho_valid = true;
-        }
         if (c->ops->step_needs_density(c->m)) {
             if ((rc = timer_begin(c, 0, &slot))) return rc;
             FLB_CUDA(c->ops->density(c->m, src, c->drho, c->stream));
@@ -576,22 +539,7 @@ static int step_impl(flb_ctx* c, int nsteps, double* dev_sums)
             FLB_CUDA(cudaEventRecord(c->zt.ev[2 * c->zt.issued], c->stream));
         }
         cudaError_t se;
-        if (nextrho) {
-            // the step, then the completion of the column ends of the parts it
-            // wrote (same column length, so before the tuning resets it)
-            int nrows = 0;
-            float* pout = c->rho_part[c->rho_cur ^ 1];
-            se = c->ops->step_next(c->m, c->step, src, dst, c->rho_part[c->rho_cur], pout, c->rho_ext,
-                                   dev_sums ? c->partials : nullptr, &nrows, c->stream);
-            if (se == cudaSuccess && dev_sums)
-                se = flb::sum_columns(c->partials, nrows, 4, dev_sums + 4 * (size_t)t, c->stream);
-            if (se == cudaSuccess && !tune) {
-                if ((rc = timer_end(c, slot))) return rc;
-                if ((rc = timer_begin(c, 0, &slot))) return rc;
-            }
-            if (se == cudaSuccess) se = c->ops->rho_fixup(c->m, pout, c->rho_ext, c->stream);
-            if (se == cudaSuccess) c->rho_cur ^= 1;
-        } else if (dev_sums) {
+        if (dev_sums) {
             int nrows = 0;
             se = c->ops->step_rows(c->m, c->step, src, dst, c->drho, c->partials, &nrows, c->stream);
             if (se == cudaErrorNotSupported) {
@@ -952,7 +900,6 @@ int flb_set_populations(flb_ctx* c, const double* f)
     int rc = alloc((void**)&d, n * sizeof(double));
     if (rc) return rc;
     cudaError_t e = cudaMemcpyAsync(d, f, n * sizeof(double), cudaMemcpyHostToDevice, c->stream);
-    c->rho_valid = false;
     if (e == cudaSuccess) e = c->ops->set_pop(c->m, d, c->buf[c->cur], c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     cudaFree(d);
@@ -974,7 +921,6 @@ int flb_set_state_device(flb_ctx* c, const void* g)
     FLB_TRACE();
     if (!c || !g) return fail(FLB_EINVAL, "ctx or g is NULL");
     DeviceGuard guard(c->device);
-    c->rho_valid = false;
     FLB_CUDA(c->ops->push_state(c->m, g, c->buf[c->cur], c->stream));
     return FLB_OK;
 }
@@ -1015,7 +961,6 @@ int flb_adjoint_segment(flb_ctx* c, const void* g_start, uint64_t step0, int n, 
     char* S = (char*)states;
     // forward: the states at step0 .. step0+n-1 (pre-collision deviations)
     FLB_CUDA(cudaMemcpyAsync(S, g_start, pb, cudaMemcpyDeviceToDevice, c->stream));
-    c->rho_valid = false;
     FLB_CUDA(c->ops->push_state(c->m, g_start, c->buf[c->cur], c->stream));
     c->step = step0;
     for (int k = 1; k < n; ++k) {
@@ -1190,7 +1135,6 @@ int flb_load(flb_ctx** out, const char* path, const flb_options* opt)
         }
     }
     c->cur = 0;
-    c->rho_valid = false;
     c->step = u64[2];
     *out = c;
     return FLB_OK;

@@ -84,17 +84,6 @@ struct PrecOps {
     // launched) where the step kernel does not provide them
     cudaError_t (*step_rows)(const HostModel&, uint64_t step, const void* src, void* dst, const void* drho,
                              double* rows, int* nrows, cudaStream_t);
-    // The force-model step that also leaves the density of the next step as
-    // per-tile parts (flb_nextrho.cuh), where nextrho(m) is 1: rho_parts
-    // computes the parts of a stored state, step_next steps from `src` with
-    // the parts part_in and writes part_out plus the column-end pieces `ext`
-    // (3 ncol (X Y + ntiles 84) floats), which rho_fixup then folds into
-    // part_out; rows as in step_rows.
-    int (*nextrho)(const HostModel&);
-    cudaError_t (*rho_parts)(const HostModel&, const void* pop, float* part, cudaStream_t);
-    cudaError_t (*step_next)(const HostModel&, uint64_t step, const void* src, void* dst, const float* part_in,
-                             float* part_out, float* ext, double* rows, int* nrows, cudaStream_t);
-    cudaError_t (*rho_fixup)(const HostModel&, float* part, const float* ext, cudaStream_t);
 };
 
 const PrecOps& ops_fp64();

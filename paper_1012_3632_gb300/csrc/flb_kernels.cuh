@@ -773,7 +773,9 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                 if (e < MPP) {
                     const int c = mc[j];
                     const F2 rc = F2(r0[c], r0[c + 1]);
-                    F2 lap(0.f);
+                    // sum_i w_i (rho_i - rho) = (1/18) (axis sum) + (1/36) (edge sum) - (2/3) rho
+                    // (the Laplacian is 6 times it)
+                    F2 sax(0.f), sed(0.f);
 #pragma unroll
                     for (int i = 1; i < L::Q; ++i) {
                         const int cz = Vel<L>::cz(i);
@@ -782,8 +784,12 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                         const int o = c + Vel<L>::cx(i) + RX * Vel<L>::cy(i);
                         const F2 v = Vel<L>::cx(i) != 0 ? mk2(*reinterpret_cast<const float2*>(pl + o))
                                                         : F2(pl[o], pl[o + 1]);
-                        lap += (float)Vel<L>::w(i) * (v - rc);
+                        if (i < 7)
+                            sax += v;
+                        else
+                            sed += v;
                     }
+                    const F2 lap = (1.0f / 18.0f) * sax + (1.0f / 36.0f) * sed - (2.0f / 3.0f) * rc;
                     const F2 d = rc + a.rho0_minus_rhoc;
                     const F2 mu = d * (a.A + a.B * (d * d)) - (6.0f * a.kappa) * lap;
                     out[2 * e] = mu.v.x;
@@ -798,21 +804,27 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
             const float* mlo = smu[mb];
             const float* mmid = smu[mb1];
             const float* mhi = smu[mb2];
-            F2 gx(0.f), gy(0.f), gz(0.f);
+            // sum_i w_i c_i mu_i (grad mu / 3; F = -3 rho times it) from the
+            // differences mu(c) - mu(-c) of the nine velocity pairs (2p-1, 2p):
+            // axis pairs weigh 1/18, edge pairs 1/36
+            F2 dp[10];
 #pragma unroll
-            for (int i = 1; i < L::Q; ++i) {
-                const int cz = Vel<L>::cz(i);
-                const float* pl = cz > 0 ? mhi : (cz < 0 ? mlo : mmid);
-                const int o = cm + Vel<L>::cx(i) + MX * Vel<L>::cy(i);
-                const F2 v = Vel<L>::cx(i) != 0 ? mk2(*reinterpret_cast<const float2*>(pl + o)) : F2(pl[o], pl[o + 1]);
-                const F2 wm = (float)Vel<L>::w(i) * v;
-                if (Vel<L>::cx(i) > 0) gx += wm;
-                if (Vel<L>::cx(i) < 0) gx = gx - wm;
-                if (Vel<L>::cy(i) > 0) gy += wm;
-                if (Vel<L>::cy(i) < 0) gy = gy - wm;
-                if (Vel<L>::cz(i) > 0) gz += wm;
-                if (Vel<L>::cz(i) < 0) gz = gz - wm;
+            for (int q = 1; q <= 9; ++q) {
+                F2 v2[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = 2 * q - 1 + h;
+                    const int cz = Vel<L>::cz(i);
+                    const float* pl = cz > 0 ? mhi : (cz < 0 ? mlo : mmid);
+                    const int o = cm + Vel<L>::cx(i) + MX * Vel<L>::cy(i);
+                    v2[h] = Vel<L>::cx(i) != 0 ? mk2(*reinterpret_cast<const float2*>(pl + o)) : F2(pl[o], pl[o + 1]);
+                }
+                dp[q] = v2[0] - v2[1];
             }
+            // pairs 4..9: (1,1,0) (1,-1,0) (1,0,1) (1,0,-1) (0,1,1) (0,1,-1)
+            const F2 gx = (1.0f / 18.0f) * dp[1] + (1.0f / 36.0f) * ((dp[4] + dp[5]) + (dp[6] + dp[7]));
+            const F2 gy = (1.0f / 18.0f) * dp[2] + (1.0f / 36.0f) * ((dp[4] - dp[5]) + (dp[8] + dp[9]));
+            const F2 gz = (1.0f / 18.0f) * dp[3] + (1.0f / 36.0f) * ((dp[6] - dp[7]) + (dp[8] - dp[9]));
             const F2 rho = a.c.rho0 + mk2(*reinterpret_cast<const float2*>(srho[ra] + cr));
             const F2 pre = -3.0f * rho;
             // pull the pair (its lines were fetched by the gather of this plane;

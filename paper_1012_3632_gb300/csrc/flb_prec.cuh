@@ -5,13 +5,11 @@
 #pragma once
 
 #include <algorithm>
-#include <mutex>
 #include <cmath>
 #include <type_traits>
 
 #include "flb_internal.h"
 #include "flb_kernels.cuh"
-#include "flb_nextrho.cuh"
 
 #ifndef FLB_MARCH_MINB
 #define FLB_MARCH_MINB 3
@@ -39,12 +37,6 @@
 #endif
 #ifndef FLB_MARCH2_TY
 #define FLB_MARCH2_TY 8
-#endif
-#ifndef FLB_NEXTRHO
-#define FLB_NEXTRHO 1
-#endif
-#ifndef FLB_NEXTRHO_MINB
-#define FLB_NEXTRHO_MINB 3
 #endif
 
 namespace flb {
@@ -566,81 +558,6 @@ struct Prec {
         return step_t<D2Q9, false, 32, 8, 1>(m, t, src, dst, drho, st);
     }
 
-    // D3Q19 force model with the excess free energy, FP32 arithmetic on FP32
-    // or BF16 storage, X % 32 == 0 and Y % 8 == 0: the step that leaves the
-    // density of the next step as per-tile parts (flb_nextrho.cuh).
-    static int nextrho(const HostModel& m)
-    {
-        if constexpr (kPackedStorage)
-            return FLB_NEXTRHO && m.Q == 19 && m.nonideal && !m.total && m.model == 0 && m.X % nr::TW == 0 &&
-                   m.Y % nr::TH == 0;
-        return 0;
-    }
-    static cudaError_t rho_parts(const HostModel& m, const void* pop, float* part, cudaStream_t st)
-    {
-        if constexpr (kPackedStorage) {
-            const dim3 g(m.X / nr::TW, m.Y / nr::TH, m.Z), b(nr::TXT, nr::TH, 1);
-            k_rho_parts<S><<<g, b, 0, st>>>(make_planes<S>(pop, nullptr, 19, m.V), part, m.X, m.Y, m.Z,
-                                             m.X / nr::TW);
-            return cudaGetLastError();
-        }
-        return cudaErrorNotSupported;
-    }
-    // k_step_nextrho takes more than 48 KB of shared memory: allow its dynamic
-    // part, once per device
-    static cudaError_t nextrho_smem_optin()
-    {
-        if constexpr (kPackedStorage) {
-            constexpr int kMaxDev = 128;
-            static bool done[kMaxDev] = {false};
-            static std::mutex mtx;
-            int dev = 0;
-            cudaError_t e = cudaGetDevice(&dev);
-            if (e != cudaSuccess) return e;
-            if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-            std::lock_guard<std::mutex> lock(mtx);
-            if (!done[dev]) {
-                e = cudaFuncSetAttribute(k_step_nextrho<S, FLB_NEXTRHO_MINB, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nr::kDynSmem);
-                if (e == cudaSuccess)
-                    e = cudaFuncSetAttribute(k_step_nextrho<S, FLB_NEXTRHO_MINB, true>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nr::kDynSmem);
-                if (e != cudaSuccess) return e;
-                done[dev] = true;
-            }
-        }
-        return cudaSuccess;
-    }
-    static cudaError_t step_next(const HostModel& m, uint64_t t, const void* src, void* dst, const float* part_in,
-                                 float* part_out, float* ext, double* rows, int* nrows, cudaStream_t st)
-    {
-        if constexpr (kPackedStorage) {
-            const StepArgs<float> a = make_args<D3Q19, float>(m, t);
-            const RhoParts rp{part_in, part_out, ext, m.X / nr::TW, m.Y / nr::TH};
-            const dim3 g(m.X / nr::TW, m.Y / nr::TH, (m.Z + a.nzc - 1) / a.nzc), b(nr::TXT, nr::TH, 1);
-            const Planes<S> pl = make_planes<S>(src, dst, 19, m.V);
-            const cudaError_t e = nextrho_smem_optin();
-            if (e != cudaSuccess) return e;
-            if (rows) {
-                *nrows = (int)(g.x * g.y * g.z);
-                k_step_nextrho<S, FLB_NEXTRHO_MINB, true><<<g, b, nr::kDynSmem, st>>>(a, pl, rp, rows);
-            } else {
-                k_step_nextrho<S, FLB_NEXTRHO_MINB><<<g, b, nr::kDynSmem, st>>>(a, pl, rp, nullptr);
-            }
-            return cudaGetLastError();
-        }
-        return cudaErrorNotSupported;
-    }
-    static cudaError_t rho_fixup(const HostModel& m, float* part, const float* ext, cudaStream_t st)
-    {
-        const int nzc = make_args<D3Q19, R>(m, 0).nzc;
-        const long ntiles = (long)(m.X / nr::TW) * (m.Y / nr::TH);
-        const long n = ((long)m.X * m.Y + ntiles * nr::NRING) * ((m.Z + nzc - 1) / nzc);
-        const long nb = std::min<long>((n + 255) / 256, 152L * 16);
-        k_rho_fixup<float><<<(unsigned)nb, 256, 0, st>>>(part, ext, m.X, m.Y, m.Z, nzc, (int)ntiles);
-        return cudaGetLastError();
-    }
-
     template <class L>
     static cudaError_t init_l(const HostModel& m, void* dst, const double* rho, const double* u, int thermal,
                               cudaStream_t st)
@@ -809,8 +726,7 @@ struct Prec {
     {
         static const PrecOps o = {(int)sizeof(S), (int)sizeof(R), density, step, init, get_pop, set_pop, moments,
                                   mu_force, mode_partials, cons_partials, mode_field, rows, needs_density,
-                                  pull_state, push_state, get_sites, step_rows, nextrho, rho_parts, step_next,
-                                  rho_fixup};
+                                  pull_state, push_state, get_sites, step_rows};
         return o;
     }
 };

@@ -1,7 +1,7 @@
 """Bounds check of the kernels' writes.  compute-sanitizer is not available on
 the GPU pool, so contexts created with guard zones (opt.guard = 1: 64 KiB of a
 fixed byte pattern before and after both population buffers and the density
-field, and the density parts of the force-model step on whole tiles) run every step path and every observable on tiny, odd and ragged
+field) run every step path and every observable on tiny, odd and ragged
 lattices -- where the periodic wrap and the partial tiles are most exposed --
 and flb_check_guards confirms that no zone was written.
 """
@@ -17,9 +17,8 @@ EXCESS = dict(A=-0.01, B=0.1, rho_c=1.0, kappa=0.02)
 TOTAL = landau_free_energy(1.0, 0.5, 0.1, 0.08)
 SWIFT = dict(TOTAL, model=1)
 
-# (32, 8, 1), (32, 16, 7), (64, 8, 18): whole 32 x 8 tiles, where the force-model
-# step also writes the next step's density parts (one-tile periodic wrap,
-# single-plane lattice, columns of several planes)
+# (32, 8, 1), (32, 16, 7), (64, 8, 18): whole 32 x 8 tiles of the force-model
+# step (one-tile periodic wrap, single-plane lattice, columns of several planes)
 D3 = [(1, 1, 1), (2, 3, 5), (4, 4, 4), (6, 5, 7), (8, 9, 17), (36, 10, 3), (34, 9, 18), (32, 8, 1), (32, 16, 7),
       (64, 8, 18)]
 D2 = [(1, 1, 1), (5, 3, 1), (32, 7, 1), (20, 12, 1)]

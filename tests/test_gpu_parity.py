@@ -248,17 +248,13 @@ def test_checkpoint_resume_is_bitwise(tmp_path, prec):
 SWIFT_FE = dict(A=-0.025, B=0.4, rho_c=0.75, kappa=0.08, total=True, model=1)
 
 
-@pytest.mark.parametrize("Q,dims,fe,gathers,zc", [(19, (32, 16, 8), FE, 6, 0), (19, (32, 16, 8), FE, 6, 1),
-                                                  (19, (34, 16, 8), FE, 0, 0), (9, (32, 16, 1), FE, 0, 0),
-                                                  (9, (32, 16, 1), SWIFT_FE, 5, 0)])
-def test_kernel_timing_counts_launches(Q, dims, fe, gathers, zc):
-    """The D3Q19 force-model step on whole 32 x 8 tiles leaves the next step's
-    density as per-tile parts: one pass over the initial state, then a small
-    launch after each step that completes the planes at the column ends;
-    elsewhere the force-model steps gather the density inside
-    the step kernel; the modified-equilibrium step reads a density field (and
-    its coloured noise) made by a launch before it."""
-    with Context(Q, dims, precision="fp32", free_energy=fe, kT=1e-6, omega_shear=1.0, z_chunk=zc) as ctx:
+@pytest.mark.parametrize("Q,dims,fe,gathers", [(19, (32, 16, 8), FE, 0), (9, (32, 16, 1), FE, 0),
+                                               (9, (32, 16, 1), SWIFT_FE, 5)])
+def test_kernel_timing_counts_launches(Q, dims, fe, gathers):
+    """The force-model steps gather the density inside the step kernel; the
+    modified-equilibrium step reads a density field (and its coloured noise)
+    made by a launch before it."""
+    with Context(Q, dims, precision="fp32", free_energy=fe, kT=1e-6, omega_shear=1.0) as ctx:
         ctx.init(rho=inputs.uniform_density(dims))
         ctx.kernel_timing(True)
         ctx.step(5)
@@ -416,8 +412,7 @@ def test_max_size_fp32_nonideal_sampled():
     sites against oracle windows."""
     dims = (1024, 1024, 1024)
     V = int(np.prod(dims))
-    parts = 2 * 4 * (V + 1024 * (1024 // 32) * (1024 // 8) * 84)  # density parts of two states
-    if _free_device_bytes() < 2 * 19 * 4 * V + 4 * V + parts + 16e9:
+    if _free_device_bytes() < 2 * 19 * 4 * V + 4 * V + 16e9:
         pytest.skip("not enough device memory")
     kw = dict(kT=1e-6, omega_shear=1.0, omega_bulk=1.0, omega_ghost=1.0, seed=3)
     ctx, p = _pair(19, dims, "fp32", FE, **kw)
@@ -456,8 +451,8 @@ def test_z_chunk_changes_no_result(prec):
 
 
 @pytest.mark.parametrize("Q,dims,prec,fe", [
-    (19, (64, 16, 20), "fp32", FE),   # step kernel's own sums, density parts
-    (19, (32, 8, 9), "bf16", FE),     # the same with BF16 storage
+    (19, (64, 16, 20), "fp32", FE),   # step kernel's own sums, whole 32 x 8 tiles
+    (19, (32, 8, 9), "bf16", FE),     # the same with BF16 storage, one tile per row
     (19, (24, 20, 70), "fp32", FE),   # step kernel's own sums, quad gather
     (19, (18, 12, 9), "bf16", FE),    # pair gather, BF16 storage
     (19, (16, 12, 10), "fp32", None),  # ideal step: reduction before each step
@@ -490,10 +485,9 @@ def test_step_sums_equal_conservation_before_each_step(Q, dims, prec, fe):
 
 
 # ---------------------------------------------------------------------------
-# The D3Q19 force-model step on whole 32 x 8 tiles (X % 32 == 0, Y % 8 == 0)
-# leaves the next step's density as per-tile parts instead of gathering it
-# again: parity, invariance and the pass that rebuilds the parts of a stored
-# state.
+# The D3Q19 force-model step on whole 32 x 8 tiles (X % 32 == 0, Y % 8 == 0,
+# the shape of the 256^3 workload): one tile per row or column (the tile its
+# own periodic neighbour), one and two planes, column ends.
 # ---------------------------------------------------------------------------
 
 TILED = [(32, 8, 12), (64, 16, 9), (32, 24, 5), (96, 8, 3), (32, 8, 1), (64, 8, 2)]
@@ -520,9 +514,8 @@ def test_bf16_nonideal_tiled(dims):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 def test_tiled_z_chunk_changes_no_result(prec):
-    """The split of the density into per-tile parts is fixed by the tiling, not
-    by the column length: columns of 1, 2, 3, 7, 16 or all 70 planes, or the
-    tuned length, give bitwise the same populations."""
+    """Columns of 1, 2, 3, 7, 16 or all 70 planes, or the tuned length, give
+    bitwise the same populations on whole tiles."""
     dims = (64, 16, 70)
     rho = inputs.uniform_density(dims, seed=4)
     kw = dict(kT=1e-6, omega_shear=1.1, omega_bulk=1.0, omega_ghost=1.2, seed=9)
@@ -542,10 +535,10 @@ def test_tiled_z_chunk_changes_no_result(prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-def test_tiled_parts_of_a_stored_state_equal_the_steps(tmp_path, prec):
-    """The parts that the step leaves and the parts rebuilt from a stored state
-    (after a checkpoint load, or after the state is written back through
-    flb_set_state_device) are bitwise the same, so the continued runs are."""
+def test_tiled_resume_is_bitwise(tmp_path, prec):
+    """A run continued from a checkpoint, or from its state written back
+    through flb_set_state_device, equals the uninterrupted run bit for bit
+    (columns of 7 planes on whole tiles)."""
     import torch
 
     dims = (64, 16, 20)
