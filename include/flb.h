@@ -260,6 +260,17 @@ int flb_check_guards(flb_ctx* ctx);
  * step.  Errors as flb_step. */
 int flb_step_sums(flb_ctx* ctx, int nsteps, double* sums);
 
+/* flb_step_sums without the wait: enqueues the nsteps steps and the copy of
+ * their sums (the same 4*nsteps doubles, mass included) into the host array
+ * sums on the context's stream and returns.  sums must stay valid and unread
+ * until the stream has been synchronised (flb_synchronize, or any call that
+ * waits for the stream); with page-locked (pinned) host memory the copy is
+ * asynchronous, with pageable memory the runtime may wait for it.  A later
+ * call reuses the same device rows only after this call's copy in stream
+ * order.  Errors as flb_step (a failed launch is reported by this call, a
+ * failure inside a kernel by the next synchronising call). */
+int flb_step_sums_async(flb_ctx* ctx, int nsteps, double* sums);
+
 /* Total mass and momentum of the current state, summed on the GPU in double:
  * out[0] = sum rho, out[1..3] = sum_r sum_i f_i c_i (z component 0 for D2Q9). */
 int flb_conservation(flb_ctx* ctx, double out[4]);

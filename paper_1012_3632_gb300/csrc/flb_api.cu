@@ -590,6 +590,40 @@ int flb_step(flb_ctx* c, int nsteps)
     return step_impl(c, nsteps, nullptr);
 }
 
+namespace {
+// sums[4 t] += m0, t < n: the total mass from the mass deviation
+__global__ void k_add_mass(double* __restrict__ sums, int n, double m0)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) sums[4 * (long)t] += m0;
+}
+}  // namespace
+
+int flb_step_sums_async(flb_ctx* c, int nsteps, double* sums)
+{
+    FLB_TRACE();
+    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(FLB_EINVAL, "nsteps must be >= 0");
+    if (nsteps > 0 && !sums) return fail(FLB_EINVAL, "sums is NULL");
+    if (nsteps == 0) return FLB_OK;
+    DeviceGuard guard(c->device);
+    int rc = ensure_partials(c);
+    if (rc) return rc;
+    if ((size_t)nsteps > c->ss_cap) {
+        if (c->ss_dev) cudaFree(c->ss_dev);
+        c->ss_dev = nullptr;
+        c->ss_cap = 0;
+        if ((rc = alloc((void**)&c->ss_dev, 4 * (size_t)nsteps * sizeof(double)))) return rc;
+        c->ss_cap = (size_t)nsteps;
+    }
+    if ((rc = step_impl(c, nsteps, c->ss_dev))) return rc;
+    k_add_mass<<<std::min((nsteps + 127) / 128, 64), 128, 0, c->stream>>>(c->ss_dev, nsteps,
+                                                                        c->m.rho0 * (double)c->m.V);
+    FLB_CUDA(cudaGetLastError());
+    FLB_CUDA(cudaMemcpyAsync(sums, c->ss_dev, 4 * (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+    return FLB_OK;
+}
+
 int flb_step_sums(flb_ctx* c, int nsteps, double* sums)
 {
     FLB_TRACE();

@@ -29,7 +29,7 @@ PRECISIONS = {"fp64": FP64, "fp32": FP32, "bf16": BF16}
 EXPORTS = [
     "flb_default_options", "flb_create", "flb_init", "flb_step", "flb_moments", "flb_structure_factor",
     "flb_snapshot_count", "flb_reset_accumulators", "flb_conservation", "flb_get_populations",
-    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_z_chunk", "flb_adjoint_segment", "flb_step_sums", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
+    "flb_set_populations", "flb_get_sites", "flb_check_guards", "flb_z_chunk", "flb_adjoint_segment", "flb_step_sums", "flb_step_sums_async", "flb_get_step", "flb_set_step", "flb_set_stream", "flb_synchronize",
     "flb_get_info", "flb_kernel_timing", "flb_kernel_times", "flb_save", "flb_load", "flb_error_string",
     "flb_last_error", "flb_destroy", "flb_structure_factor_noalloc",
     "flb_batch_create", "flb_batch_init", "flb_batch_step", "flb_batch_autotune", "flb_batch_mode_variance",
@@ -115,6 +115,7 @@ def lib():
         "flb_z_chunk": (ctypes.c_int, [vp, ip, ip]),
         "flb_adjoint_segment": (ctypes.c_int, [vp, vp, ctypes.c_uint64, ctypes.c_int, vp, vp, vp]),
         "flb_step_sums": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "flb_step_sums_async": (ctypes.c_int, [vp, ctypes.c_int, dp]),
         "flb_get_step": (ctypes.c_int, [vp, P(ctypes.c_uint64)]),
         "flb_set_step": (ctypes.c_int, [vp, ctypes.c_uint64]),
         "flb_set_stream": (ctypes.c_int, [vp, vp]),
@@ -247,6 +248,15 @@ class Context:
         sums = out if out is not None else np.empty((nsteps, 4))
         _check(lib().flb_step_sums(self._h, int(nsteps), _dptr(sums)))
         return sums
+
+    def step_sums_async(self, nsteps: int, out: np.ndarray) -> np.ndarray:
+        """nsteps steps whose (nsteps, 4) sums land in `out` (a C-contiguous
+        float64 array, ideally in page-locked memory) once the context's
+        stream has been synchronised; returns without waiting."""
+        if out.dtype != np.float64 or not out.flags.c_contiguous or out.size < 4 * nsteps:
+            raise ValueError("out must be a C-contiguous float64 array of at least 4 * nsteps elements")
+        _check(lib().flb_step_sums_async(self._h, int(nsteps), _dptr(out)))
+        return out
 
     def get_populations(self) -> np.ndarray:
         f = np.empty((self.Q, self.V))

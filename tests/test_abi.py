@@ -92,6 +92,7 @@ def test_null_context_rejected(flb):
     calls = [
         lambda: L.flb_step(None, 1),
         lambda: L.flb_step_sums(None, 1, d),
+        lambda: L.flb_step_sums_async(None, 1, d),
         lambda: L.flb_conservation(None, d),
         lambda: L.flb_get_populations(None, d),
         lambda: L.flb_get_sites(None, ll, 2, d),

@@ -482,6 +482,19 @@ def test_step_sums_equal_conservation_before_each_step(Q, dims, prec, fe):
     want = np.array(want)
     assert np.abs(got[:, 0] - want[:, 0]).max() <= 1e-12 * V + 1e-5
     assert np.abs(got[:, 1:] - want[:, 1:]).max() <= 1e-5
+    # the same steps with flb_step_sums_async, one step per call into a
+    # page-locked array read after one wait: the same sums and populations
+    import torch
+
+    pinned = torch.empty((n, 4), dtype=torch.float64, pin_memory=True).numpy()
+    with Context(Q, dims, free_energy=fe, **kw) as c:
+        c.init(rho=rho)
+        for t in range(n):
+            c.step_sums_async(1, pinned[t])
+        c.synchronize()
+        fc = c.get_populations()
+    assert np.array_equal(fc, fb)
+    assert np.array_equal(pinned, got)
 
 
 # ---------------------------------------------------------------------------
