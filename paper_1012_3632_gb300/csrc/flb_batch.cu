@@ -12,6 +12,7 @@
 #include <cstring>
 #include <map>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/flb.h"
@@ -25,8 +26,10 @@ Coll<float> coll_fp32(const HostModel& m, uint64_t step);
 
 namespace {
 
-// Tile shapes (x, y, z), 256 sites each, powers of two.
-constexpr int kShapes[][3] = {{32, 8, 1}, {32, 4, 2}, {32, 2, 4}, {16, 16, 1}, {16, 8, 2}, {16, 4, 4}, {8, 8, 4}};
+// Tile shapes (x, y, z), 256 sites each, powers of two (x at least 2: one
+// site pair per thread along x).
+constexpr int kShapes[][3] = {{32, 8, 1}, {32, 4, 2}, {32, 2, 4}, {16, 16, 1}, {16, 8, 2}, {16, 4, 4}, {8, 8, 4},
+                              {64, 4, 1}, {64, 2, 2}, {64, 1, 4}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 struct BatchRep {
@@ -53,18 +56,25 @@ struct Tile {
 // 128 threads per tile of tx*ty*tz = 256 sites: one thread per site pair
 // (x, x+1) along x when the replica's X is even (packed FP32 arithmetic, as the
 // single-lattice kernel k_step2), otherwise one site per thread in two passes.
+// OFF32: every replica has 19 V < 2^31, so a population's element offset from
+// its replica's base fits in 32 bits (one address operation per access).
+template <bool OFF32>
 __global__ void __launch_bounds__(128) k_step_batch(const __grid_constant__ BatchArgs A, const int4* __restrict__ tiles,
                                                     int ntiles, const unsigned long long* __restrict__ d_step)
 {
+    using Off = typename std::conditional<OFF32, int, long>::type;
     using L = D3Q19;
     const uint32_t step = (uint32_t)__ldg(d_step);
+    // the next work item is fetched one iteration ahead, off the path of the pulls
+    int4 w_next = (int)blockIdx.x < ntiles ? __ldg(tiles + blockIdx.x) : make_int4(0, 0, 0, 0);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int4 w = __ldg(tiles + t);
+        const int4 w = w_next;
+        if (t + (int)gridDim.x < ntiles) w_next = __ldg(tiles + t + gridDim.x);
         const BatchRep& B = A.rep[w.x];
         const float* src = A.src + B.off;
         float* dst = A.dst + B.off;
         const int X = B.X, Y = B.Y, Z = B.Z;
-        const long V = (long)X * Y * Z;
+        const Off V = (Off)X * Y * Z;
         if ((X & 1) == 0) {
             const int hx = B.tx >> 1;  // pairs per tile row
             const int x = w.y * B.tx + 2 * (threadIdx.x & (hx - 1));
@@ -77,7 +87,7 @@ __global__ void __launch_bounds__(128) k_step_batch(const __grid_constant__ Batc
             F2 g[L::Q];
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) {
-                const float* p = src + (long)i * V + X * (yv[1 - Vel<L>::cy(i)] + Y * zv[1 - Vel<L>::cz(i)]);
+                const float* p = src + ((Off)i * V + X * (yv[1 - Vel<L>::cy(i)] + Y * zv[1 - Vel<L>::cz(i)]));
                 const int cx = Vel<L>::cx(i);
                 if (cx == 0)
                     g[i] = mk2(ld_stream2(p + x));
@@ -89,7 +99,7 @@ __global__ void __launch_bounds__(128) k_step_batch(const __grid_constant__ Batc
             const int s = x + X * (y + Y * z);
             L::template collide<false>(g, F2(0.f), F2(0.f), F2(0.f), B.c, (uint32_t)s, step);
 #pragma unroll
-            for (int i = 0; i < L::Q; ++i) __stcs(reinterpret_cast<float2*>(dst + (long)i * V + s), g[i].v);
+            for (int i = 0; i < L::Q; ++i) __stcs(reinterpret_cast<float2*>(dst + ((Off)i * V + s)), g[i].v);
         } else {
             for (int half = 0; half < 2; ++half) {
                 const int q = threadIdx.x + 128 * half;
@@ -101,11 +111,11 @@ __global__ void __launch_bounds__(128) k_step_batch(const __grid_constant__ Batc
                 float g[L::Q];
 #pragma unroll
                 for (int i = 0; i < L::Q; ++i)
-                    g[i] = src[(long)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i))];
+                    g[i] = src[(Off)i * V + nb.src(Vel<L>::cx(i), Vel<L>::cy(i), Vel<L>::cz(i))];
                 const int s = x + X * (y + Y * z);
                 L::template collide<false>(g, 0.f, 0.f, 0.f, B.c, (uint32_t)s, step);
 #pragma unroll
-                for (int i = 0; i < L::Q; ++i) __stcs(dst + (long)i * V + s, g[i]);
+                for (int i = 0; i < L::Q; ++i) __stcs(dst + ((Off)i * V + s), g[i]);
             }
         }
     }
@@ -144,6 +154,7 @@ struct flb_batch {
     int4* tiles = nullptr;
     int ntiles = 0;
     int grid = 0;
+    bool off32 = true;                // every replica: 19 V < 2^31 (k_step_batch<true>)
     BatchArgs args[2];                // src/dst for cur = 0 and cur = 1
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     // reductions
@@ -236,7 +247,10 @@ int build_tiles(flb_batch* b)
 
 int launch_step(flb_batch* b, cudaStream_t st)
 {
-    flb::k_step_batch<<<b->grid, 128, 0, st>>>(b->args[b->cur], b->tiles, b->ntiles, b->d_step);
+    if (b->off32)
+        flb::k_step_batch<true><<<b->grid, 128, 0, st>>>(b->args[b->cur], b->tiles, b->ntiles, b->d_step);
+    else
+        flb::k_step_batch<false><<<b->grid, 128, 0, st>>>(b->args[b->cur], b->tiles, b->ntiles, b->d_step);
     flb::k_advance<<<1, 1, 0, st>>>(b->d_step);
     BCUDA(cudaGetLastError());
     return FLB_OK;
@@ -329,6 +343,7 @@ int flb_batch_create(flb_batch** out, int lattice, int n, const int* dims, const
         b->off[r] = b->total;
         b->total += 19LL * m.V;
         b->sites += m.V;
+        if (19LL * m.V >= (1LL << 31)) b->off32 = false;
         b->shape[r] = (m.X % 32 == 0) ? 1 : 4;  // (32,4,2) or (16,8,2) until tuned
     }
     b->mv_sum.assign((size_t)n * 19, 0.0);
@@ -350,7 +365,10 @@ int flb_batch_create(flb_batch** out, int lattice, int n, const int* dims, const
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flb::k_step_batch, 128, 0);
+    if (b->off32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flb::k_step_batch<true>, 128, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, flb::k_step_batch<false>, 128, 0);
     b->grid = std::max(1, nsm * std::max(1, per_sm));
     if ((rc = build_tiles(b))) return cleanup(rc);
     *out = b;
@@ -434,8 +452,14 @@ int flb_batch_autotune(flb_batch* b, int* shapes_out)
             float ms = 0.f;
             for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // first launch warms up
                 cudaEventRecord(e0, b->stream);
-                for (int it = 0; it < 5; ++it)
-                    flb::k_step_batch<<<b->grid, 128, 0, b->stream>>>(b->args[b->cur], d_t, (int)t.size(), b->d_step);
+                for (int it = 0; it < 5; ++it) {
+                    if (b->off32)
+                        flb::k_step_batch<true>
+                            <<<b->grid, 128, 0, b->stream>>>(b->args[b->cur], d_t, (int)t.size(), b->d_step);
+                    else
+                        flb::k_step_batch<false>
+                            <<<b->grid, 128, 0, b->stream>>>(b->args[b->cur], d_t, (int)t.size(), b->d_step);
+                }
                 cudaEventRecord(e1, b->stream);
                 e = cudaEventSynchronize(e1);
                 float m1 = 0.f;
