@@ -513,10 +513,11 @@ int flb_init(flb_ctx* c, const double* rho, const double* u, int thermal_init)
 
 // The time steps of flb_step; with dev_sums (device, 4 doubles per step) also
 // the sums of the state each step starts from: the step kernel's own partial
-// sums where it provides them, else the conservation reduction before the step.
-// dev_sums[0] holds the mass deviation (the caller adds rho0 V).
+// sums where it provides them, else the conservation reduction before the step
+// (dev_sums[4 t] is the total mass: rho0 V is added to the summed deviations).
 static int step_impl(flb_ctx* c, int nsteps, double* dev_sums)
 {
+    const double m0 = c->m.rho0 * (double)c->m.V;
     for (int t = 0; t < nsteps; ++t) {
         const void* src = c->buf[c->cur];
         void* dst = c->buf[c->cur ^ 1];
@@ -545,10 +546,10 @@ static int step_impl(flb_ctx* c, int nsteps, double* dev_sums)
             if (se == cudaErrorNotSupported) {
                 // this step kernel has no partial sums: reduce the state first
                 FLB_CUDA(c->ops->cons_partials(c->m, src, c->partials, &nrows, c->stream));
-                FLB_CUDA(flb::sum_columns(c->partials, nrows, 4, dev_sums + 4 * (size_t)t, c->stream));
+                FLB_CUDA(flb::sum_columns(c->partials, nrows, 4, dev_sums + 4 * (size_t)t, c->stream, m0));
                 se = c->ops->step(c->m, c->step, src, dst, c->drho, c->stream);
             } else if (se == cudaSuccess) {
-                se = flb::sum_columns(c->partials, nrows, 4, dev_sums + 4 * (size_t)t, c->stream);
+                se = flb::sum_columns(c->partials, nrows, 4, dev_sums + 4 * (size_t)t, c->stream, m0);
             }
         } else {
             se = c->ops->step(c->m, c->step, src, dst, c->drho, c->stream);
@@ -590,14 +591,6 @@ int flb_step(flb_ctx* c, int nsteps)
     return step_impl(c, nsteps, nullptr);
 }
 
-namespace {
-// sums[4 t] += m0, t < n: the total mass from the mass deviation
-__global__ void k_add_mass(double* __restrict__ sums, int n, double m0)
-{
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) sums[4 * (long)t] += m0;
-}
-}  // namespace
-
 int flb_step_sums_async(flb_ctx* c, int nsteps, double* sums)
 {
     FLB_TRACE();
@@ -616,9 +609,6 @@ int flb_step_sums_async(flb_ctx* c, int nsteps, double* sums)
         c->ss_cap = (size_t)nsteps;
     }
     if ((rc = step_impl(c, nsteps, c->ss_dev))) return rc;
-    k_add_mass<<<std::min((nsteps + 127) / 128, 64), 128, 0, c->stream>>>(c->ss_dev, nsteps,
-                                                                        c->m.rho0 * (double)c->m.V);
-    FLB_CUDA(cudaGetLastError());
     FLB_CUDA(cudaMemcpyAsync(sums, c->ss_dev, 4 * (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost,
                              c->stream));
     return FLB_OK;
@@ -645,8 +635,6 @@ int flb_step_sums(flb_ctx* c, int nsteps, double* sums)
     FLB_CUDA(cudaMemcpyAsync(sums, c->ss_dev, 4 * (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost,
                              c->stream));
     FLB_CUDA(cudaStreamSynchronize(c->stream));
-    const double m0 = c->m.rho0 * (double)c->m.V;
-    for (int t = 0; t < nsteps; ++t) sums[4 * t] += m0;
     return FLB_OK;
 }
 

@@ -509,12 +509,20 @@ struct D3Q19 {
     }
 
     // FORCE = false: F = 0 (ideal gas); the force terms are not evaluated.
+    // first (optional): receives the pre-collision mass deviation and
+    // momentum m[0..3] = sum_i g_i, sum_i c_i g_i the collision forms anyway.
     template <bool FORCE = true, class R, class PR>
     __device__ __forceinline__ static void collide(R g[19], R Fx, R Fy, R Fz, const Coll<PR>& P, uint32_t site,
-                                                   uint32_t step)
+                                                   uint32_t step, R* first = nullptr)
     {
         R m[19];
         moments(g, m);
+        if (first) {
+            first[0] = m[0];
+            first[1] = m[1];
+            first[2] = m[2];
+            first[3] = m[3];
+        }
         const R rho = P.rho0 + m[0];
         const R ir = rcp_(rho);
         R ux, uy, uz;

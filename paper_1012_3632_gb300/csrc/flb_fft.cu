@@ -14,7 +14,8 @@ namespace flb {
 // ---------------------------------------------------------------------------
 // Column sums (one block per column, fixed order: deterministic)
 // ---------------------------------------------------------------------------
-__global__ void k_sum_columns(const double* __restrict__ partials, int nrows, int ncol, double* __restrict__ out)
+__global__ void k_sum_columns(const double* __restrict__ partials, int nrows, int ncol, double* __restrict__ out,
+                              double add0)
 {
     __shared__ double sh[256];
     const int c = blockIdx.x;
@@ -26,12 +27,12 @@ __global__ void k_sum_columns(const double* __restrict__ partials, int nrows, in
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[c] = sh[0];
+    if (threadIdx.x == 0) out[c] = c == 0 ? sh[0] + add0 : sh[0];
 }
 
-cudaError_t sum_columns(const double* partials, int nrows, int ncol, double* out, cudaStream_t s)
+cudaError_t sum_columns(const double* partials, int nrows, int ncol, double* out, cudaStream_t s, double add0)
 {
-    k_sum_columns<<<ncol, 256, 0, s>>>(partials, nrows, ncol, out);
+    k_sum_columns<<<ncol, 256, 0, s>>>(partials, nrows, ncol, out, add0);
     return cudaGetLastError();
 }
 

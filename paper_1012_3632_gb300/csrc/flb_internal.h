@@ -90,8 +90,10 @@ const PrecOps& ops_fp64();
 const PrecOps& ops_fp32();
 const PrecOps& ops_bf16();
 
-// Deterministic column sums: out[c] = sum_r partials[r*ncol + c] (flb_fft.cu).
-cudaError_t sum_columns(const double* partials, int nrows, int ncol, double* out, cudaStream_t s);
+// Deterministic column sums: out[c] = sum_r partials[r*ncol + c], plus add0
+// on column 0 (flb_fft.cu).
+cudaError_t sum_columns(const double* partials, int nrows, int ncol, double* out, cudaStream_t s,
+                        double add0 = 0.0);
 
 // True when an axis of length L is transformed by the in-place mixed-radix FFT
 // (L a product of 2, 3 and 5, at most 4096); other lengths need `scratch`.

@@ -648,9 +648,10 @@ __global__ void __launch_bounds__(TX* TY, MINB)
 // runs through k_step_march.
 // ---------------------------------------------------------------------------
 // SUMS: the block also adds up the mass deviation and the momentum of the
-// state it steps from -- the density of each collided site from the density
-// ring, sum_i c_i g_i from its pulled populations -- and writes them as one
-// row of 4 doubles (rows[block * 4 + 0..3]; FP32 within a warp, FP64 above).
+// state it steps from -- sum_i g_i and sum_i c_i g_i of each collided site's
+// pulled populations, the first moments its collision forms -- and writes
+// them as one row of 4 doubles (rows[block * 4 + 0..3]; FP32 within a warp,
+// FP64 above).
 template <class S, int TXT, int TY, int MINB, int GX, bool SUMS = false>
 __global__ void __launch_bounds__(TXT* TY, MINB)
     k_step_march2(const StepArgs<float> a, const __grid_constant__ Planes<S> P, double* __restrict__ rows)
@@ -844,20 +845,18 @@ __global__ void __launch_bounds__(TXT* TY, MINB)
                 else
                     g[i] = F2(A::plain1(p + x + 1), A::plain1(p + x2));
             }
-            if constexpr (SUMS) {
-                sum_r += mk2(*reinterpret_cast<const float2*>(srho[ra] + cr));
-#pragma unroll
-                for (int i = 1; i < L::Q; ++i) {
-                    if (Vel<L>::cx(i) > 0) sum_jx += g[i];
-                    if (Vel<L>::cx(i) < 0) sum_jx = sum_jx - g[i];
-                    if (Vel<L>::cy(i) > 0) sum_jy += g[i];
-                    if (Vel<L>::cy(i) < 0) sum_jy = sum_jy - g[i];
-                    if (Vel<L>::cz(i) > 0) sum_jz += g[i];
-                    if (Vel<L>::cz(i) < 0) sum_jz = sum_jz - g[i];
-                }
-            }
             const int s = x + X * y + XY * z;
-            L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
+            if constexpr (SUMS) {
+                // the pre-collision mass deviation and momentum the collision forms
+                F2 first[4];
+                L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step, first);
+                sum_r += first[0];
+                sum_jx += first[1];
+                sum_jy += first[2];
+                sum_jz += first[3];
+            } else {
+                L::collide(g, pre * gx, pre * gy, pre * gz, a.c, (uint32_t)s, a.c.step);
+            }
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) A::store2(P.dst[i] + s, g[i].v);
         }
