@@ -255,9 +255,9 @@ int flb_check_guards(flb_ctx* ctx);
  * sums: host, 4*nsteps doubles, written when the call returns (it waits for
  * the context's stream once, at the end).  The D3Q19 force-model step with
  * FP32 or BF16 storage and even X forms these sums inside the step kernel
- * (per-block partial sums of the density it holds and of the populations it
- * pulls); every other step runs the reduction of flb_conservation before the
- * step.  Errors as flb_step. */
+ * (per-block partial sums of the mass deviation and momentum its collision
+ * forms from the pulled populations); every other step runs the reduction of
+ * flb_conservation before the step.  Errors as flb_step. */
 int flb_step_sums(flb_ctx* ctx, int nsteps, double* sums);
 
 /* flb_step_sums without the wait: enqueues the nsteps steps and the copy of
