@@ -500,6 +500,8 @@ def main():
     ap.add_argument("--workload", default="nonideal256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-replica comparison")
+    ap.add_argument("--batched-replicas", type=int, default=64, help="replicas of the batched ensemble")
+    ap.add_argument("--batched-steps", type=int, default=2000, help="ensemble steps with snapshots")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WORKLOADS[args.workload]
@@ -671,7 +673,7 @@ def main():
         "clocks": clk.summary(), "e2e": e2e, "gpu_launches": n_launch,
     }
     if not args.no_batched:
-        line["batched"] = batched_vs_plain()
+        line["batched"] = batched_vs_plain(n=args.batched_replicas, steps=args.batched_steps)
         line["adjoint"] = adjoint_vs_plain()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl)
