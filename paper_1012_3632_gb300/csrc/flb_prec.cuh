@@ -10,7 +10,6 @@
 
 #include "flb_internal.h"
 #include "flb_kernels.cuh"
-#include "flb_ws.cuh"
 
 #ifndef FLB_MARCH_MINB
 #define FLB_MARCH_MINB 3
@@ -38,17 +37,6 @@
 #endif
 #ifndef FLB_MARCH2_TY
 #define FLB_MARCH2_TY 8
-#endif
-// Warp-specialised non-ideal step (lattices of whole 32 x 16 tiles) and its
-// lookahead in planes.
-#ifndef FLB_STEP_WS
-#define FLB_STEP_WS 0
-#endif
-#ifndef FLB_WS_DL
-#define FLB_WS_DL 3
-#endif
-#ifndef FLB_WS_PF
-#define FLB_WS_PF 2
 #endif
 
 namespace flb {
@@ -521,13 +509,6 @@ struct Prec {
         if (m.Q == 19) {
             if (m.nonideal) {
                 if constexpr (kPackedStorage) {
-                    if (FLB_STEP_WS && !rows && FLB_PACKED && !m.total && m.X % kWsTileX == 0 &&
-                        m.Y % kWsTileY == 0) {
-                        const StepArgs<R> a = make_args<D3Q19, R>(m, t);
-                        const dim3 g(m.X / kWsTileX, m.Y / kWsTileY, (m.Z + a.nzc - 1) / a.nzc);
-                        k_step_ws<S, FLB_WS_DL, FLB_WS_PF><<<g, kWsThreads, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
-                        return cudaGetLastError();
-                    }
                     if (m.X % 2 == 0 && FLB_PACKED && !m.total) {
                         constexpr int TXT = 16, TY = FLB_MARCH2_TY;
                         const StepArgs<R> a = make_args<D3Q19, R>(m, t);
