@@ -92,20 +92,55 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K)
     return c;
 }
 
+// SFU approximations (PTX lg2/rsqrt/rcp/sin/cos .approx.ftz.f32).  Their
+// arguments here are normal numbers, for which the flush-to-zero forms give
+// the same results; they skip the handling of subnormal operands, which took
+// a third of the Box-Muller transform's instructions.
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sin_approx(float x)
+{
+    float y;
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float cos_approx(float x)
+{
+    float y;
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Box-Muller on a pair of 32-bit words; uniforms (x + 1/2) 2^-32 lie in (0, 1].
-// Single precision uses the SFU intrinsics: log via __logf, the radius via
+// Single precision on the SFU: -2 ln u0 = (-2 ln 2) log2 u0, the radius via
 // rsqrt, and cos/sin(2 pi u) = -cos/-sin(2 pi u - pi) with the argument in
-// [-pi, pi] where __sincosf is accurate to 2^-21.4 absolute.
+// [-pi, pi], where the approximate sine and cosine are accurate to about
+// 2^-21 absolute.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1)
 {
     const float u0 = fmaf(__uint2float_rn(a), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
     const float u1 = fmaf(__uint2float_rn(b), 2.3283064365386963e-10f, 1.1641532182693481e-10f);
-    const float t = fmaxf(-2.0f * __logf(u0), 1e-30f);  // u0 may round to 1: radius 0, not NaN
-    const float r = t * rsqrtf(t);
-    float s, c;
-    __sincosf(fmaf(u1, 6.28318530717958648f, -3.14159265358979324f), &s, &c);
-    z0 = -r * c;
-    z1 = -r * s;
+    const float t = fmaxf(-1.3862943611198906f * lg2_approx(u0), 1e-30f);  // u0 may round to 1: radius 0, not NaN
+    const float r = t * rsqrt_approx(t);
+    const float w = fmaf(u1, 6.28318530717958648f, -3.14159265358979324f);
+    z0 = -r * cos_approx(w);
+    z1 = -r * sin_approx(w);
 }
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double& z0, double& z1)
 {
@@ -188,10 +223,10 @@ __device__ __forceinline__ F2& operator*=(F2& a, F2 b)
 // reciprocal and square root: the FP32 paths use the SFU approximations (the
 // density is ~1 and the results feed terms far below FP32 storage rounding)
 __device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
-__device__ __forceinline__ float rcp_(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ F2 rcp_(F2 x) { return F2(__fdividef(1.0f, x.v.x), __fdividef(1.0f, x.v.y)); }
+__device__ __forceinline__ float rcp_(float x) { return rcp_approx(x); }
+__device__ __forceinline__ F2 rcp_(F2 x) { return F2(rcp_approx(x.v.x), rcp_approx(x.v.y)); }
 __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-__device__ __forceinline__ float sqrt_(float x) { return x * rsqrtf(x); }
+__device__ __forceinline__ float sqrt_(float x) { return x * rsqrt_approx(x); }
 __device__ __forceinline__ F2 sqrt_(F2 x) { return F2(sqrt_(x.v.x), sqrt_(x.v.y)); }
 
 // Normals 0..N-1 of the collision noise of `site` (one site per lane).
