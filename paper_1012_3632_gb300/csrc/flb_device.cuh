@@ -237,15 +237,38 @@ __device__ __forceinline__ void noise_normals(const PhiloxKeys& K, uint32_t site
 #pragma unroll
     for (int b = 0; b < NCALL; ++b) normals4(K, site, step, (uint32_t)b, rep, z + 4 * b);
 }
+// Box-Muller of two sites at once: the word pairs (a0, a1) of site x and
+// (b0, b1) of site x+1, the same arithmetic as box_muller with the FP32 steps
+// in packed form (bitwise the same normals; the SFU steps stay per element).
+__device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1, F2& z0, F2& z1)
+{
+    const float2 sc = make_float2(2.3283064365386963e-10f, 2.3283064365386963e-10f);
+    const float2 of = make_float2(1.1641532182693481e-10f, 1.1641532182693481e-10f);
+    const float2 u0 = __ffma2_rn(make_float2(__uint2float_rn(a0), __uint2float_rn(b0)), sc, of);
+    const float2 u1 = __ffma2_rn(make_float2(__uint2float_rn(a1), __uint2float_rn(b1)), sc, of);
+    const float2 l = __fmul2_rn(make_float2(-1.3862943611198906f, -1.3862943611198906f),
+                                make_float2(lg2_approx(u0.x), lg2_approx(u0.y)));
+    const float2 t = make_float2(fmaxf(l.x, 1e-30f), fmaxf(l.y, 1e-30f));
+    const float2 r = __fmul2_rn(t, make_float2(rsqrt_approx(t.x), rsqrt_approx(t.y)));
+    const float2 w = __ffma2_rn(u1, make_float2(6.28318530717958648f, 6.28318530717958648f),
+                                make_float2(-3.14159265358979324f, -3.14159265358979324f));
+    const float2 nr = make_float2(-r.x, -r.y);
+    z0 = mk2(__fmul2_rn(nr, make_float2(cos_approx(w.x), cos_approx(w.y))));
+    z1 = mk2(__fmul2_rn(nr, make_float2(sin_approx(w.x), sin_approx(w.y))));
+}
+// The normals of the two sites (site, site + 1) of a thread: site's in .x,
+// site + 1's in .y.
 template <int NCALL>
 __device__ __forceinline__ void noise_normals(const PhiloxKeys& K, uint32_t site, uint32_t step, uint32_t rep,
                                               F2 z[4 * NCALL])
 {
-    float a[4 * NCALL], b[4 * NCALL];
-    noise_normals<NCALL>(K, site, step, rep, a);
-    noise_normals<NCALL>(K, site + 1, step, rep, b);
 #pragma unroll
-    for (int k = 0; k < 4 * NCALL; ++k) z[k] = F2(a[k], b[k]);
+    for (int b = 0; b < NCALL; ++b) {
+        const uint4 ra = philox4x32_10(make_uint4(site, step, (uint32_t)b, rep), K);
+        const uint4 rb = philox4x32_10(make_uint4(site + 1, step, (uint32_t)b, rep), K);
+        box_muller2(ra.x, ra.y, rb.x, rb.y, z[4 * b], z[4 * b + 1]);
+        box_muller2(ra.z, ra.w, rb.z, rb.w, z[4 * b + 2], z[4 * b + 3]);
+    }
 }
 
 // ---------------------------------------------------------------------------
