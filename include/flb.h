@@ -417,7 +417,7 @@ void flb_batch_destroy(flb_batch* b);
  * process exits.  The first call on a device sets that device up: with the
  * device current it looks up the array's device address
  * (cudaGetSymbolAddress), reads the SM count and raises the FFT kernel's
- * shared-memory limit; make that first call before any stream capture.  The
+ * shared-memory limit (host-side runtime calls; none of them allocates).  The
  * look-up is kept for the life of the process: after a cudaDeviceReset in the
  * caller's process this entry point must not be called again.  Every call
  * uses the same array, which keeps the last call's contents (each call
