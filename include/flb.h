@@ -143,7 +143,7 @@ typedef struct {
                             kernels' writes for debugging; default 0) */
     int z_chunk;         /* D3Q19 non-ideal step (z-marching kernels): planes of z per
                             thread block.  0 (default): flb_step times candidate
-                            lengths on its first steps (two launches each, CUDA
+                            lengths on its first steps (three launches each, CUDA
                             events, one host wait on them when done) and keeps
                             the fastest; > 0: that length (at most Z).  The chunk
                             length changes no result: every site's arithmetic is

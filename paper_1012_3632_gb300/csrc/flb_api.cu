@@ -256,9 +256,12 @@ int reduce_to_host(flb_ctx* c, int nrows, int ncol, double* host)
 
 // z-chunk autotuning of the z-marching step (D3Q19 non-ideal, opt.z_chunk = 0).
 // Candidates: for every block count nc from ceil(Z/40) to ceil(Z/12) the
-// balanced length ceil(Z/nc), at most 16 of them; each is launched twice with
-// CUDA events around it and the fastest launch decides.  The steps are the
+// balanced length ceil(Z/nc), at most 16 of them; each is launched
+// kZTuneRounds times (the candidates in turn) with CUDA events around it and
+// the fastest launch decides.  The steps are the
 // caller's own steps: the chunk length changes no result.
+constexpr int kZTuneRounds = 3;
+
 void ztune_start(flb_ctx* c)
 {
     const HostModel& m = c->m;
@@ -272,7 +275,7 @@ void ztune_start(flb_ctx* c)
     const size_t n = std::min<size_t>(all.size(), 16);
     for (size_t k = 0; k < n; ++k) cand.push_back(all[k * all.size() / n]);
     if (cand.size() < 2) return;
-    std::vector<cudaEvent_t> ev(4 * cand.size());
+    std::vector<cudaEvent_t> ev(2 * kZTuneRounds * cand.size());
     for (auto& e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) {
             for (auto& f : ev)
@@ -558,7 +561,7 @@ static int step_impl(flb_ctx* c, int nsteps, double* dev_sums)
             c->m.zchunk = 0;
             FLB_CUDA(se);
             FLB_CUDA(cudaEventRecord(c->zt.ev[2 * c->zt.issued + 1], c->stream));
-            if (++c->zt.issued == (int)(2 * c->zt.cand.size()) && (rc = ztune_finish(c))) return rc;
+            if (++c->zt.issued == (int)(kZTuneRounds * c->zt.cand.size()) && (rc = ztune_finish(c))) return rc;
         }
         FLB_CUDA(se);
         if ((rc = timer_end(c, slot))) return rc;

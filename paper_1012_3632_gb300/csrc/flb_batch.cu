@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(128) k_step_batch(const __grid_constant__ Batc
                     g[i] = F2(ld_stream1(p + x + 1), ld_stream1(p + x2));
             }
             const int s = x + X * (y + Y * z);
-            L::template collide<false>(g, F2(0.f), F2(0.f), F2(0.f), B.c, (uint32_t)s, step);
+            L::template collide<false, true>(g, F2(0.f), F2(0.f), F2(0.f), B.c, (uint32_t)s, step);
 #pragma unroll
             for (int i = 0; i < L::Q; ++i) __stcs(reinterpret_cast<float2*>(dst + ((Off)i * V + s)), g[i].v);
         } else {

@@ -14,6 +14,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_bf16.h>
 
 namespace flb {
@@ -90,6 +91,15 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys& K)
                        (uint32_t)p0);
     }
     return c;
+}
+
+// One round of philox4x32_10 with round keys k0, k1 (for callers that run
+// several counters' rounds in lock-step).
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1)
+{
+    const unsigned long long p0 = 0xD2511F53ull * c.x;
+    const unsigned long long p1 = 0xCD9E8D57ull * c.z;
+    return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
 }
 
 // SFU approximations (PTX lg2/rsqrt/rcp/sin/cos .approx.ftz.f32).  Their
@@ -257,17 +267,41 @@ __device__ __forceinline__ void box_muller2(uint32_t a0, uint32_t a1, uint32_t b
     z1 = mk2(__fmul2_rn(nr, make_float2(sin_approx(w.x), sin_approx(w.y))));
 }
 // The normals of the two sites (site, site + 1) of a thread: site's in .x,
-// site + 1's in .y.
-template <int NCALL>
+// site + 1's in .y.  INTERLEAVED: the rounds of all 2 NCALL Philox calls in
+// lock-step (round-major) rather than one call after another -- the same
+// numbers; which order schedules better depends on the kernel around it.
+template <int NCALL, bool INTERLEAVED = false>
 __device__ __forceinline__ void noise_normals(const PhiloxKeys& K, uint32_t site, uint32_t step, uint32_t rep,
                                               F2 z[4 * NCALL])
 {
+    if constexpr (INTERLEAVED) {
+        uint4 ca[NCALL], cb[NCALL];
 #pragma unroll
-    for (int b = 0; b < NCALL; ++b) {
-        const uint4 ra = philox4x32_10(make_uint4(site, step, (uint32_t)b, rep), K);
-        const uint4 rb = philox4x32_10(make_uint4(site + 1, step, (uint32_t)b, rep), K);
-        box_muller2(ra.x, ra.y, rb.x, rb.y, z[4 * b], z[4 * b + 1]);
-        box_muller2(ra.z, ra.w, rb.z, rb.w, z[4 * b + 2], z[4 * b + 3]);
+        for (int b = 0; b < NCALL; ++b) {
+            ca[b] = make_uint4(site, step, (uint32_t)b, rep);
+            cb[b] = make_uint4(site + 1, step, (uint32_t)b, rep);
+        }
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+#pragma unroll
+            for (int b = 0; b < NCALL; ++b) {
+                ca[b] = philox_round(ca[b], K.k[r], K.k[10 + r]);
+                cb[b] = philox_round(cb[b], K.k[r], K.k[10 + r]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < NCALL; ++b) {
+            box_muller2(ca[b].x, ca[b].y, cb[b].x, cb[b].y, z[4 * b], z[4 * b + 1]);
+            box_muller2(ca[b].z, ca[b].w, cb[b].z, cb[b].w, z[4 * b + 2], z[4 * b + 3]);
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < NCALL; ++b) {
+            const uint4 ra = philox4x32_10(make_uint4(site, step, (uint32_t)b, rep), K);
+            const uint4 rb = philox4x32_10(make_uint4(site + 1, step, (uint32_t)b, rep), K);
+            box_muller2(ra.x, ra.y, rb.x, rb.y, z[4 * b], z[4 * b + 1]);
+            box_muller2(ra.z, ra.w, rb.z, rb.w, z[4 * b + 2], z[4 * b + 3]);
+        }
     }
 }
 
@@ -569,7 +603,8 @@ struct D3Q19 {
     // FORCE = false: F = 0 (ideal gas); the force terms are not evaluated.
     // first (optional): receives the pre-collision mass deviation and
     // momentum m[0..3] = sum_i g_i, sum_i c_i g_i the collision forms anyway.
-    template <bool FORCE = true, class R, class PR>
+    // INTERLEAVED: the two-site noise draws its Philox calls round-major.
+    template <bool FORCE = true, bool INTERLEAVED = false, class R, class PR>
     __device__ __forceinline__ static void collide(R g[19], R Fx, R Fy, R Fz, const Coll<PR>& P, uint32_t site,
                                                    uint32_t step, R* first = nullptr)
     {
@@ -624,7 +659,10 @@ struct D3Q19 {
         if (P.noise) {
             const R sr = P.noise_local ? sqrt_(rho) : R(P.sqrt_rho0);
             R z[16];
-            noise_normals<4>(P.key, site, step, P.replica, z);
+            if constexpr (std::is_same<R, F2>::value)
+                noise_normals<4, INTERLEAVED>(P.key, site, step, P.replica, z);
+            else
+                noise_normals<4>(P.key, site, step, P.replica, z);
 #pragma unroll
             for (int k = 0; k < 15; ++k) Dm[4 + k] += P.ns[k] * (sr * z[k]);
         }
