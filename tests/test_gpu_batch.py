@@ -3,7 +3,7 @@ uneven sizes in one persistent launch per step, replayed from a CUDA graph.
 
 Each replica must evolve exactly like a single lattice with the same
 parameters, Philox key and replica word: checked against the FP64 oracle and
-against a single-lattice context."""
+against a single-lattice context (bit for bit where X is even)."""
 import numpy as np
 import pytest
 
@@ -35,7 +35,12 @@ def test_batch_replicas_match_oracle_and_single_lattice():
             with Context(19, dims, precision="fp32", replica=r, **kw) as c:
                 c.init(thermal=True)
                 c.step(steps)
-                assert np.abs(got - c.get_populations()).max() <= 1e-6, r
+                if dims[0] % 2 == 0:
+                    # the two-site path: packed FP32 with the same operations
+                    # in the same order as the single-lattice step
+                    assert np.array_equal(got, c.get_populations()), r
+                else:
+                    assert np.abs(got - c.get_populations()).max() <= 1e-6, r
 
 
 def test_graph_replays_equal_single_steps():
