@@ -253,22 +253,26 @@ int flb_check_guards(flb_ctx* ctx);
  * momentum of the state the step starts from: sums[4*t + 0] = sum rho,
  * sums[4*t + 1..3] = sum_r sum_i f_i c_i (as flb_conservation), t < nsteps.
  * sums: host, 4*nsteps doubles, written when the call returns (it waits for
- * the context's stream once, at the end).  The D3Q19 force-model step with
+ * the context's stream once, at the end; device-addressable page-locked
+ * memory is written in place by the reduction, other memory through a copy).  The D3Q19 force-model step with
  * FP32 or BF16 storage and even X forms these sums inside the step kernel
  * (per-block partial sums of the mass deviation and momentum its collision
  * forms from the pulled populations); every other step runs the reduction of
  * flb_conservation before the step.  Errors as flb_step. */
 int flb_step_sums(flb_ctx* ctx, int nsteps, double* sums);
 
-/* flb_step_sums without the wait: enqueues the nsteps steps and the copy of
- * their sums (the same 4*nsteps doubles, mass included) into the host array
- * sums on the context's stream and returns.  sums must stay valid and unread
- * until the stream has been synchronised (flb_synchronize, or any call that
- * waits for the stream); with page-locked (pinned) host memory the copy is
- * asynchronous, with pageable memory the runtime may wait for it.  A later
- * call reuses the same device rows only after this call's copy in stream
- * order.  Errors as flb_step (a failed launch is reported by this call, a
- * failure inside a kernel by the next synchronising call). */
+/* flb_step_sums without the wait: enqueues the nsteps steps and the delivery
+ * of their sums (the same 4*nsteps doubles, mass included) into the host
+ * array sums on the context's stream and returns.  sums must stay valid and
+ * unread until the stream has been synchronised (flb_synchronize, or any call
+ * that waits for the stream).  Page-locked host memory that the device can
+ * address (cudaHostAlloc / cudaMallocHost, or registered, under unified
+ * addressing) receives the sums straight from the reduction kernel; other
+ * memory gets them by a copy from device rows on the stream (asynchronous for
+ * page-locked memory; with pageable memory the runtime may wait for it), and
+ * a later call reuses those rows only after this call's copy in stream order.
+ * Errors as flb_step (a failed launch is reported by this call, a failure
+ * inside a kernel by the next synchronising call). */
 int flb_step_sums_async(flb_ctx* ctx, int nsteps, double* sums);
 
 /* Total mass and momentum of the current state, summed on the GPU in double:

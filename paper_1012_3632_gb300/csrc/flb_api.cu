@@ -594,16 +594,26 @@ int flb_step(flb_ctx* c, int nsteps)
     return step_impl(c, nsteps, nullptr);
 }
 
-int flb_step_sums_async(flb_ctx* c, int nsteps, double* sums)
+// Page-locked host memory that the device can address (cudaHostAlloc'd or
+// registered memory under unified addressing): the column sums are written
+// straight into it, with no copy on the stream.  NULL for other memory.
+static double* device_alias(const double* host)
 {
-    FLB_TRACE();
-    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
-    if (nsteps < 0) return fail(FLB_EINVAL, "nsteps must be >= 0");
-    if (nsteps > 0 && !sums) return fail(FLB_EINVAL, "sums is NULL");
-    if (nsteps == 0) return FLB_OK;
-    DeviceGuard guard(c->device);
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, host) != cudaSuccess) {
+        cudaGetLastError();  // pageable memory may report an error: not an alias
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer ? static_cast<double*>(at.devicePointer) : nullptr;
+}
+
+// The steps with their sums into `sums` (host): written in place when the
+// device can address it, else staged on the device and copied on the stream.
+static int step_sums_to_host(flb_ctx* c, int nsteps, double* sums)
+{
     int rc = ensure_partials(c);
     if (rc) return rc;
+    if (double* alias = device_alias(sums)) return step_impl(c, nsteps, alias);
     if ((size_t)nsteps > c->ss_cap) {
         if (c->ss_dev) cudaFree(c->ss_dev);
         c->ss_dev = nullptr;
@@ -617,6 +627,17 @@ int flb_step_sums_async(flb_ctx* c, int nsteps, double* sums)
     return FLB_OK;
 }
 
+int flb_step_sums_async(flb_ctx* c, int nsteps, double* sums)
+{
+    FLB_TRACE();
+    if (!c) return fail(FLB_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(FLB_EINVAL, "nsteps must be >= 0");
+    if (nsteps > 0 && !sums) return fail(FLB_EINVAL, "sums is NULL");
+    if (nsteps == 0) return FLB_OK;
+    DeviceGuard guard(c->device);
+    return step_sums_to_host(c, nsteps, sums);
+}
+
 int flb_step_sums(flb_ctx* c, int nsteps, double* sums)
 {
     FLB_TRACE();
@@ -625,18 +646,8 @@ int flb_step_sums(flb_ctx* c, int nsteps, double* sums)
     if (nsteps > 0 && !sums) return fail(FLB_EINVAL, "sums is NULL");
     if (nsteps == 0) return FLB_OK;
     DeviceGuard guard(c->device);
-    int rc = ensure_partials(c);
+    int rc = step_sums_to_host(c, nsteps, sums);
     if (rc) return rc;
-    if ((size_t)nsteps > c->ss_cap) {
-        if (c->ss_dev) cudaFree(c->ss_dev);
-        c->ss_dev = nullptr;
-        c->ss_cap = 0;
-        if ((rc = alloc((void**)&c->ss_dev, 4 * (size_t)nsteps * sizeof(double)))) return rc;
-        c->ss_cap = (size_t)nsteps;
-    }
-    if ((rc = step_impl(c, nsteps, c->ss_dev))) return rc;
-    FLB_CUDA(cudaMemcpyAsync(sums, c->ss_dev, 4 * (size_t)nsteps * sizeof(double), cudaMemcpyDeviceToHost,
-                             c->stream));
     FLB_CUDA(cudaStreamSynchronize(c->stream));
     return FLB_OK;
 }

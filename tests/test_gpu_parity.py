@@ -495,6 +495,19 @@ def test_step_sums_equal_conservation_before_each_step(Q, dims, prec, fe):
         fc = c.get_populations()
     assert np.array_equal(fc, fb)
     assert np.array_equal(pinned, got)
+    # both deliveries: page-locked memory written in place by the reduction
+    # (synchronous call), pageable memory through the copy (asynchronous call)
+    pinned2 = torch.empty((n, 4), dtype=torch.float64, pin_memory=True).numpy()
+    pageable = np.empty((n, 4))
+    with Context(Q, dims, free_energy=fe, **kw) as d:
+        d.init(rho=rho)
+        d.step_sums(n // 2, out=pinned2[: n // 2])
+        d.step_sums_async(n - n // 2, pageable[n // 2:])
+        d.synchronize()
+        fd = d.get_populations()
+    assert np.array_equal(fd, fb)
+    assert np.array_equal(pinned2[: n // 2], got[: n // 2])
+    assert np.array_equal(pageable[n // 2:], got[n // 2:])
 
 
 # ---------------------------------------------------------------------------
