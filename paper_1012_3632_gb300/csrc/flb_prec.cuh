@@ -29,8 +29,14 @@
 #ifndef FLB_STEP2_TZ
 #define FLB_STEP2_TZ 2
 #endif
+// Ideal-gas two-site step, minimum resident blocks per SM: 5 with FP32
+// storage (96 registers, 48 bytes spilled, 20 warps per SM: measured faster
+// than 4 blocks at 126 registers), 4 with BF16 storage (5 measured slower).
 #ifndef FLB_STEP2_MINB
-#define FLB_STEP2_MINB 4
+#define FLB_STEP2_MINB 5
+#endif
+#ifndef FLB_STEP2_MINB_BF16
+#define FLB_STEP2_MINB_BF16 4
 #endif
 #ifndef FLB_MARCH2_MINB
 #define FLB_MARCH2_MINB 3
@@ -546,7 +552,8 @@ struct Prec {
                     const StepArgs<R> a = make_args<D3Q19, R>(m, t);
                     const dim3 b(TXT, TY, TZ);
                     const dim3 g((m.X / 2 + TXT - 1) / TXT, (m.Y + TY - 1) / TY, (m.Z + TZ - 1) / TZ);
-                    k_step2<D3Q19, S, TXT, TY, TZ, FLB_STEP2_MINB>
+                    constexpr int MINB = sizeof(S) == 4 ? FLB_STEP2_MINB : FLB_STEP2_MINB_BF16;
+                    k_step2<D3Q19, S, TXT, TY, TZ, MINB>
                         <<<g, b, 0, st>>>(a, make_planes<S>(src, dst, 19, m.V));
                     return cudaGetLastError();
                 }
